@@ -1,0 +1,144 @@
+/*
+ * fdas.h -- C ABI of the GB300 (sm_103a) FDAS frequency-domain convolution library.
+ *
+ * The library computes the filter-output plane of the Fourier-domain acceleration
+ * search (Sec. 3): one long complex single-precision Fourier-domain array x[0..N)
+ * is convolved with a bank of M complex FIR templates h_z[0..K) (Eq. 1,
+ * y_z[i] = sum_{k<K} x[i-k] h_z[k], i = 0..N-1, x[j] = 0 for j < 0), and the
+ * spectral power P[z][i] = |y_z[i]|^2 is stored (Sec. 4.3: power, no square root).
+ * The convolution is evaluated by overlap-save (Algorithm 2, Sec. 3.2.2) with one
+ * forward FFT per input segment shared by all templates (Table 1 and its text).
+ *
+ * Conventions
+ *   - complex64 = two IEEE float32 (re, im), interleaved, 8 bytes per value;
+ *   - the power plane is float32, row-major [M][n]: row z holds template z in the
+ *     order the templates were given to fdas_plan_create;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream);
+ *   - device pointers belong to the caller and must stay valid until the work
+ *     queued on the stream has finished; the plan owns only its own device state;
+ *   - every entry point returns 0 (FDAS_OK) or a negative FDAS_ERR_* code and never
+ *     throws; fdas_last_error() gives a thread-local message for the last failure.
+ *   - entry points that enqueue GPU work are asynchronous unless stated otherwise.
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDAS_OK                 0
+#define FDAS_ERR_INVALID_ARG   (-1)   /* null pointer, size out of range, misaligned pointer */
+#define FDAS_ERR_OOM           (-2)   /* a device or pinned-host allocation failed */
+#define FDAS_ERR_CUDA          (-3)   /* a CUDA runtime/driver call failed (see fdas_last_error) */
+#define FDAS_ERR_TIMEOUT       (-4)   /* a bounded wait (host deadline or in-kernel spin) ran out */
+#define FDAS_ERR_BUSY          (-5)   /* server: no free slot or budget right now */
+#define FDAS_ERR_REJECTED      (-6)   /* server: request can never fit the memory budget */
+#define FDAS_ERR_UNSUPPORTED   (-7)   /* option value not built into this library */
+
+/* Arithmetic forms of the segment FFTs. */
+#define FDAS_PREC_FP32          0     /* FP32 CUDA-core FFTs (default) */
+#define FDAS_PREC_TC_BF16X3     1     /* tensor-core DFT-GEMM stages, bf16 hi/lo split, FP32 accumulate */
+
+typedef struct fdas_plan_s *fdas_plan;
+
+/* Plan options; a zero-initialised struct (or NULL) selects the defaults. */
+typedef struct {
+    int seg_len;      /* L, the overlap-save FFT length: 1024, 2048 or 4096 (0 = 2048) */
+    int tpl_per_cta;  /* G, templates per thread block: 1..M (0 = all M) */
+    int precision;    /* FDAS_PREC_* (0 = FP32) */
+    int autotune;     /* reserved for the batched form's tuner; 0 = off */
+} fdas_opts;
+
+/* Read-only description of a plan. */
+typedef struct {
+    int64_t n_max;        /* largest array length accepted */
+    int     n_templates;  /* M */
+    int     tpl_len;      /* K as given */
+    int     frame_len;    /* K used internally (K, or K+1 with a trailing zero tap when K is even) */
+    int     seg_len;      /* L */
+    int     seg_step;     /* S: valid outputs per segment, a multiple of 4, <= L - frame_len + 1 */
+    int     tpl_per_cta;  /* G */
+    int     precision;    /* FDAS_PREC_* */
+    int     device;       /* CUDA device ordinal the plan lives on */
+    int64_t device_bytes; /* device memory owned by the plan */
+} fdas_plan_desc;
+
+/*
+ * fdas_plan_create -- build a plan for arrays of up to n_max points.
+ *
+ *   templates_c64_host : host pointer, complex64 [n_templates][tpl_len], row-major.
+ *                        Copied during the call; the caller keeps ownership.
+ *   n_templates        : M >= 1.   tpl_len : K, 1 <= K <= L - 4.
+ *   opts               : NULL or options (see fdas_opts).
+ *
+ * Synchronous.  Allocates on the current CUDA device and runs the plan-time kernels:
+ * the FP64 twiddle tables and the FP64 transform of every zero-padded template,
+ * H_z = FFT_L(h_z) / L (Algorithm 2, "Fourier transform of coefficient array"; its
+ * cost is left out of Table 1 because N >> K), stored as FP32 in the order the
+ * segment kernel consumes it.
+ * Errors: INVALID_ARG (bad sizes or options), UNSUPPORTED, OOM, CUDA.
+ */
+int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates_c64_host,
+                     int n_templates, int tpl_len, const fdas_opts *opts);
+
+/* Fill *desc with the plan's parameters.  Errors: INVALID_ARG. */
+int fdas_plan_describe(fdas_plan p, fdas_plan_desc *desc);
+
+/*
+ * fdas_convolve -- power plane of one array (the hot path).
+ *
+ *   in_c64_dev    : device pointer, complex64 [n], 16-byte aligned.
+ *   n             : 1 <= n <= n_max.
+ *   out_power_dev : device pointer, float32 [M][n] row-major, 4-byte aligned; every
+ *                   element is written.  Must not overlap the input.
+ *
+ * Enqueues one kernel launch on `stream` and returns without waiting.  Per segment
+ * of L points (step S, preceded by K-1 zeros for the first, zero-filled past n):
+ * one forward FFT, then for each template the element-wise product, the inverse
+ * FFT, the discard of the first K-1 points and the power (Algorithm 2, Sec. 4.3).
+ * Errors: INVALID_ARG, CUDA (launch failure).  Asynchronous faults surface on the
+ * stream; bounded in-kernel waits that run out are reported by fdas_plan_status.
+ */
+int fdas_convolve(fdas_plan p, const void *in_c64_dev, int64_t n, float *out_power_dev,
+                  void *stream);
+
+/*
+ * fdas_convolve_host -- the same computation from and to host memory.
+ *
+ *   in_c64_host    : host complex64 [n];  out_power_host : host float32 [M][n].
+ *   Pinned (page-locked) buffers give full copy bandwidth; pageable ones work.
+ *
+ * Synchronous: copies the input to plan-owned device staging memory (allocated on
+ * the first call, sized for n_max), runs the segment kernel in chunks and copies
+ * each finished chunk of the plane back while the next one is computed, and
+ * returns once out_power_host is complete.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *out_power_host,
+                       void *stream);
+
+/*
+ * fdas_plan_status -- wait for `stream`, then read and clear the plan's device
+ * status word.  Returns FDAS_OK, FDAS_ERR_TIMEOUT if an in-kernel bounded wait ran
+ * out since the last call, or FDAS_ERR_CUDA if the stream reports an error.
+ */
+int fdas_plan_status(fdas_plan p, void *stream);
+
+/* Free the plan.  The caller must have synchronised every stream that used it. */
+int fdas_destroy(fdas_plan p);
+
+/* Static description of an FDAS_* code. */
+const char *fdas_strerror(int code);
+
+/* Thread-local message of the most recent failure on the calling thread ("" if none). */
+const char *fdas_last_error(void);
+
+/* Library version string. */
+const char *fdas_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDAS_H */

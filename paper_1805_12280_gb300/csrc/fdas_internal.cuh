@@ -1,0 +1,66 @@
+// Internal declarations shared by the plan layer and the kernels.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdas.h"
+
+namespace fdas {
+
+// ---------------------------------------------------------------------------
+// Segment FFT geometry.  L = 16 * Q * R points, NT = L / 16 threads, 16 values per
+// thread.  Forward transform (decimation in frequency over the digits of n):
+//   pass A  thread t = b*R + c holds x[a*NT + t], a < 16 -> 16-point DFT over a (k1),
+//           twiddle W_L^{t k1};
+//   pass B  thread holds (k1, c) groups, DFT over b (k2), twiddle W_{QR}^{c k2};
+//   pass C  thread holds (k1, k2) groups, DFT over c (k3);
+// X[k1 + 16 k2 + 16 Q k3] ends in registers ("C distribution").  The inverse runs
+// the same passes backwards with conjugate twiddles and ends in natural order.
+// ---------------------------------------------------------------------------
+template <int L>
+struct Geo {
+    static_assert(L == 1024 || L == 2048 || L == 4096, "segment length");
+    static constexpr int P = 16;
+    static constexpr int Q = (L == 1024) ? 8 : 16;
+    static constexpr int R = (L == 4096) ? 16 : 8;
+    static constexpr int NT = L / 16;
+    static constexpr int GB = 16 / Q;     // (k1, c) groups per thread in pass B
+    static constexpr int GC = 16 / R;     // (k1, k2) groups per thread in pass C
+    static constexpr int LD2 = NT + 1;    // padded row of the second exchange buffer
+};
+
+// Frequency index held in register slot j (0..15) of thread tau in the C distribution.
+__host__ __device__ inline int freq_of_slot(int L, int tau, int j)
+{
+    const int Q = (L == 1024) ? 8 : 16;
+    const int R = (L == 4096) ? 16 : 8;
+    const int NT = L / 16;
+    const int g = j / R, k3 = j % R;
+    const int k1 = tau & 15;
+    const int k2 = tau / 16 + (NT / 16) * g;
+    return k1 + 16 * k2 + 16 * Q * k3;
+}
+
+// Arguments of the FP32 segment kernel.
+struct OlsArgs {
+    const float4 *H;      // [M][8][NT] float4 = two complex per thread slot pair
+    const float2 *tw;     // [L] W_L^e = exp(-2 pi i e / L), FP32
+    float *out;           // [M][n]
+    int64_t n;
+    int M, G, S, K;       // templates, templates per CTA, segment step, frame length
+    int seg_begin;        // first segment of this launch
+    int *status;          // device status word (bit 0: a bounded wait ran out)
+};
+
+// Launch the FP32 segment kernel over segments [seg_begin, seg_begin + nseg).
+cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, int nseg,
+                            cudaStream_t s);
+size_t ols_fp32_smem_bytes(int L);
+
+// Plan-time kernels (FP64).
+cudaError_t launch_twiddles(int L, double2 *w64, float2 *w32, cudaStream_t s);
+cudaError_t launch_pretransform(int L, const float2 *h32, int M, int K, const double2 *w64,
+                                float4 *Hperm, cudaStream_t s);
+
+}  // namespace fdas

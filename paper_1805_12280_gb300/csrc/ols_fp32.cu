@@ -1,0 +1,219 @@
+// Fused FP32 overlap-save segment kernel (Algorithm 2 with the forward FFT shared by
+// all templates, Table 1 text; power output, Sec. 4.3).
+//
+// One thread block of NT = L/16 threads owns one input segment and a group of G
+// templates:
+//   1. TMA loads the L-point segment x[s*S - (K-1) .. s*S - (K-1) + L) into shared
+//      memory; the tensor map zero-fills before 0 (the K-1 leading zeros of the first
+//      segment) and past n;
+//   2. forward FFT (passes A, B, C; two shared-memory exchanges), the spectrum stays
+//      in registers for the whole template loop;
+//   3. per template: element-wise product with the pre-transformed template (read
+//      from L2, layout matched to the register distribution), inverse FFT (passes
+//      C', B', A'; two exchanges; 1/L is folded into the template), discard of the
+//      first K-1 points, |y|^2, coalesced stores of the valid S points.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "fdas_internal.cuh"
+#include "fft_regs.cuh"
+#include "ptx.cuh"
+
+namespace fdas {
+
+template <int L>
+struct Smem {
+    static constexpr size_t seg_bytes = sizeof(float2) * L;                   // segment / exchange 1
+    static constexpr size_t e2_bytes = sizeof(float2) * 16 * Geo<L>::LD2;    // exchange 2
+    static constexpr size_t total = 128 + seg_bytes + e2_bytes + 16;          // + alignment + mbarrier
+};
+
+template <int L, int MINB>
+__global__ void __launch_bounds__(L / 16, MINB)
+    ols_fp32_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a)
+{
+    using Gm = Geo<L>;
+    constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
+    constexpr int MASK = L - 1;
+
+    extern __shared__ unsigned char smem_raw[];
+    float2 *e1 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2 *e2 = e1 + L;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(e2 + 16 * LD2);
+
+    const int tid = threadIdx.x;
+    const int seg = a.seg_begin + blockIdx.x;
+    const int z0 = blockIdx.y * a.G;
+    const int z1 = min(z0 + a.G, a.M);
+    const int k1 = tid & 15;
+    const int hi = tid >> 4;
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(L * sizeof(float2)));
+        const int c0 = seg * a.S - (a.K - 1);
+#pragma unroll
+        for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, bar);
+    }
+
+    // Inverse-transform twiddles, fixed for this thread across all templates.
+    float2 tw1[16], tw2[16];
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        const int k2 = hi + (NT / 16) * g;
+#pragma unroll
+        for (int c = 0; c < R; ++c) tw1[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & MASK]));
+    }
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) tw2[g * Q + b] = cconj(__ldg(&a.tw[((b * R + cg) * k1) & MASK]));
+    }
+
+    const bool ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (!ok) {
+        atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+        return;
+    }
+
+    float2 v[16], X[16];
+    // ---- forward pass A: 16-point DFT over the top digit, twiddle W_L^{t k1}
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = e1[j * NT + tid];
+    dft<16, -1>(v);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(&a.tw[(tid * k) & MASK]));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) e2[tid + LD2 * k] = v[k];
+    __syncthreads();
+    // ---- forward pass B: Q-point DFT over b, twiddle W_{QR}^{c k2}
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) v[g * Q + b] = e2[(b * R + cg) + LD2 * k1];
+    }
+    dft<Q, -1, 1, 0>(v);
+    if constexpr (GB == 2) dft<Q, -1, 1, Q>(v);
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+            const float2 w = (k2 == 0) ? make_float2(1.f, 0.f) : __ldg(&a.tw[(16 * cg * k2) & MASK]);
+            e1[k1 + 16 * k2 + 16 * Q * cg] = cmul(v[g * Q + k2], w);
+        }
+    }
+    __syncthreads();
+    // ---- forward pass C: R-point DFT over c; spectrum stays in registers
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        const int k2 = hi + (NT / 16) * g;
+#pragma unroll
+        for (int c = 0; c < R; ++c) X[g * R + c] = e1[k1 + 16 * k2 + 16 * Q * c];
+    }
+    dft<R, -1, 1, 0>(X);
+    if constexpr (GC == 2) dft<R, -1, 1, R>(X);
+    __syncthreads();   // every thread has read e1 before the template loop rewrites it
+
+    const int64_t seg_out = (int64_t)seg * a.S;                 // first output index of this segment
+    const int64_t nvalid64 = a.n - seg_out;
+    const int nvalid = nvalid64 < a.S ? (int)nvalid64 : a.S;
+    const int km1 = a.K - 1;
+
+    for (int z = z0; z < z1; ++z) {
+        // ---- element-wise product with H_z (1/L folded in)
+        const float4 *Hz = a.H + (size_t)z * 8 * NT;
+#pragma unroll
+        for (int jp = 0; jp < 8; ++jp) {
+            const float4 h = __ldg(&Hz[jp * NT + tid]);
+            v[2 * jp] = cmul(X[2 * jp], make_float2(h.x, h.y));
+            v[2 * jp + 1] = cmul(X[2 * jp + 1], make_float2(h.z, h.w));
+        }
+        // ---- inverse pass C': R-point IDFT over k3, twiddle conj W_{QR}^{c k2}
+        dft<R, 1, 1, 0>(v);
+        if constexpr (GC == 2) dft<R, 1, 1, R>(v);
+#pragma unroll
+        for (int g = 0; g < GC; ++g) {
+            const int k2 = hi + (NT / 16) * g;
+#pragma unroll
+            for (int c = 0; c < R; ++c)
+                e1[k1 + 16 * k2 + 16 * Q * c] = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
+        }
+        __syncthreads();
+        // ---- inverse pass B': Q-point IDFT over k2, twiddle conj W_L^{(bR + c) k1}
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int cg = hi + (NT / 16) * g;
+#pragma unroll
+            for (int k2 = 0; k2 < Q; ++k2) v[g * Q + k2] = e1[k1 + 16 * k2 + 16 * Q * cg];
+        }
+        dft<Q, 1, 1, 0>(v);
+        if constexpr (GB == 2) dft<Q, 1, 1, Q>(v);
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int cg = hi + (NT / 16) * g;
+#pragma unroll
+            for (int b = 0; b < Q; ++b) e2[(b * R + cg) + LD2 * k1] = cmul(v[g * Q + b], tw2[g * Q + b]);
+        }
+        __syncthreads();
+        // ---- inverse pass A': 16-point IDFT over k1 -> natural order y[a*NT + t]
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = e2[tid + LD2 * k];
+        dft<16, 1>(v);
+        // ---- discard the first K-1 points, power, store
+        float *orow = a.out + (size_t)z * (size_t)a.n + seg_out;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int o = j * NT + tid - km1;
+            if (o >= 0 && o < nvalid) orow[o] = cabs2(v[j]);
+        }
+    }
+}
+
+template <int L>
+static cudaError_t launch_l(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
+{
+    constexpr int MINB = (L == 4096) ? 1 : (L == 2048 ? 3 : 6);
+    auto kern = ols_fp32_kernel<L, MINB>;
+    const size_t smem = Smem<L>::total;
+    static bool attr_set[64] = {};   // the attribute is per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    dim3 grid(nseg, (a.M + a.G - 1) / a.G);
+    kern<<<grid, L / 16, smem, s>>>(*tmap, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
+{
+    switch (L) {
+    case 1024: return launch_l<1024>(tmap, a, nseg, s);
+    case 2048: return launch_l<2048>(tmap, a, nseg, s);
+    case 4096: return launch_l<4096>(tmap, a, nseg, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t ols_fp32_smem_bytes(int L)
+{
+    switch (L) {
+    case 1024: return Smem<1024>::total;
+    case 2048: return Smem<2048>::total;
+    case 4096: return Smem<4096>::total;
+    default: return 0;
+    }
+}
+
+}  // namespace fdas

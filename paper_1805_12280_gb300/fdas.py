@@ -1,0 +1,201 @@
+"""Thin ctypes binding of ``libfdas.so`` (include/fdas.h).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  The low-level functions keep the C names; ``Plan`` wraps them for
+torch tensors (torch supplies device memory and streams).  There is no CPU
+fallback: if the library cannot be built or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+FDAS_OK = 0
+FDAS_ERR_INVALID_ARG = -1
+FDAS_ERR_OOM = -2
+FDAS_ERR_CUDA = -3
+FDAS_ERR_TIMEOUT = -4
+FDAS_ERR_BUSY = -5
+FDAS_ERR_REJECTED = -6
+FDAS_ERR_UNSUPPORTED = -7
+
+FDAS_PREC_FP32 = 0
+FDAS_PREC_TC_BF16X3 = 1
+
+
+class FdasError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__(f"{where}: {message} (code {code})")
+        self.code = code
+
+
+class fdas_opts(ctypes.Structure):
+    _fields_ = [("seg_len", ctypes.c_int), ("tpl_per_cta", ctypes.c_int),
+                ("precision", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class fdas_plan_desc(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int64), ("n_templates", ctypes.c_int), ("tpl_len", ctypes.c_int),
+                ("frame_len", ctypes.c_int), ("seg_len", ctypes.c_int), ("seg_step", ctypes.c_int),
+                ("tpl_per_cta", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
+                ("device_bytes", ctypes.c_int64)]
+
+
+# Every exported symbol with (restype, argtypes).  The CPU tests check that the
+# library exports exactly what include/fdas.h declares.
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "fdas_plan_create": (_I, [ctypes.POINTER(_P), _I64, _P, _I, _I, ctypes.POINTER(fdas_opts)]),
+    "fdas_plan_describe": (_I, [_P, ctypes.POINTER(fdas_plan_desc)]),
+    "fdas_convolve": (_I, [_P, _P, _I64, _P, _P]),
+    "fdas_convolve_host": (_I, [_P, _P, _I64, _P, _P]),
+    "fdas_plan_status": (_I, [_P, _P]),
+    "fdas_destroy": (_I, [_P]),
+    "fdas_strerror": (ctypes.c_char_p, [_I]),
+    "fdas_last_error": (ctypes.c_char_p, []),
+    "fdas_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_needed and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"CUDA library {_build.LIB} is missing; run paper_1805_12280_gb300._build.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != FDAS_OK:
+        lib = load()
+        raise FdasError(rc, where, lib.fdas_last_error().decode() or lib.fdas_strerror(rc).decode())
+
+
+# ---- the C entry points, same names ---------------------------------------
+
+def fdas_plan_create(n_max: int, templates_ptr: int, n_templates: int, tpl_len: int,
+                     opts: fdas_opts | None = None) -> int:
+    lib = load()
+    h = _P()
+    _check(lib.fdas_plan_create(ctypes.byref(h), int(n_max), _P(templates_ptr), int(n_templates), int(tpl_len),
+                                ctypes.byref(opts) if opts is not None else None), "fdas_plan_create")
+    return h.value
+
+
+def fdas_plan_describe(plan: int) -> fdas_plan_desc:
+    d = fdas_plan_desc()
+    _check(load().fdas_plan_describe(_P(plan), ctypes.byref(d)), "fdas_plan_describe")
+    return d
+
+
+def fdas_convolve(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().fdas_convolve(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_convolve")
+
+
+def fdas_convolve_host(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().fdas_convolve_host(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_convolve_host")
+
+
+def fdas_plan_status(plan: int, stream: int = 0) -> None:
+    _check(load().fdas_plan_status(_P(plan), _P(stream)), "fdas_plan_status")
+
+
+def fdas_destroy(plan: int) -> None:
+    _check(load().fdas_destroy(_P(plan)), "fdas_destroy")
+
+
+def fdas_version() -> str:
+    return load().fdas_version().decode()
+
+
+# ---- convenience wrapper for torch tensors ---------------------------------
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Plan:
+    """A plan for arrays of up to ``n_max`` points and a fixed template bank.
+
+    ``templates``: complex64 array [M, K] (host).  Options map to ``fdas_opts``.
+    """
+
+    def __init__(self, templates, n_max: int, seg_len: int = 2048, tpl_per_cta: int = 0,
+                 precision: int = FDAS_PREC_FP32, autotune: int = 0):
+        t = np.ascontiguousarray(np.atleast_2d(templates), dtype=np.complex64)
+        self.n_templates, self.tpl_len = t.shape
+        opts = fdas_opts(seg_len, tpl_per_cta, precision, autotune)
+        self.handle = fdas_plan_create(n_max, t.ctypes.data, self.n_templates, self.tpl_len, opts)
+        self.desc = fdas_plan_describe(self.handle)
+
+    def convolve(self, x, out=None, stream=None):
+        """Power plane of device array ``x`` (torch complex64, [n]) into ``out`` ([M, n] float32)."""
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        n = x.numel()
+        if out is None:
+            out = torch.empty((self.n_templates, n), dtype=torch.float32, device=x.device)
+        if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != self.n_templates * n:
+            raise ValueError("out must be a contiguous float32 tensor with M*n elements")
+        fdas_convolve(self.handle, x.data_ptr(), n, out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def convolve_host(self, x: np.ndarray, out: np.ndarray | None = None, stream=0) -> np.ndarray:
+        """Synchronous host-to-host form (host input, host plane)."""
+        x = np.ascontiguousarray(x, dtype=np.complex64)
+        n = x.size
+        if out is None:
+            out = np.empty((self.n_templates, n), dtype=np.float32)
+        if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != self.n_templates * n:
+            raise ValueError("out must be a C-contiguous float32 array with M*n elements")
+        fdas_convolve_host(self.handle, x.ctypes.data, n, out.ctypes.data,
+                           stream if isinstance(stream, int) else _stream_handle(stream))
+        return out
+
+    def status(self, stream=None) -> None:
+        fdas_plan_status(self.handle, _stream_handle(stream))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            fdas_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
