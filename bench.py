@@ -189,7 +189,7 @@ def run_reference(args):
 
 
 def workload_config(args, n, tpl_len):
-    return {"workload": f"single SKA-sized array: N=2^22 complex64, 85 templates (<= {tpl_len} taps), "
+    return {"workload": f"single SKA-sized array: N=2^{int(np.log2(n))} complex64, 85 templates (<= {tpl_len} taps), "
                         f"L={args.seg_len} overlap-save, fp32 power plane",
             "n": n, "templates": 85, "tpl_len": tpl_len, "seg_len": args.seg_len,
             "tpl_per_cta": args.tpl_per_cta or 85, "precision": "fp32",
@@ -206,7 +206,7 @@ def run_fdas(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = synth.single_ska(seed=1 + rank)            # each rank its own dedispersion trial
+    spec = synth.single_ska(n=1 << args.log2n, seed=1 + rank)   # each rank its own dedispersion trial
     x = synth.make_input(spec)
     h, _ = synth.template_bank()
     n, m = x.size, h.shape[0]
@@ -324,10 +324,11 @@ def profile_traffic():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fdas", "reference"], default="fdas")
     ap.add_argument("--seg-len", type=int, default=2048)
+    ap.add_argument("--log2n", type=int, default=22, help="array length 2^log2n (22 = the SKA-sized workload)")
     ap.add_argument("--tpl-per-cta", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -25,7 +25,8 @@ template <int L>
 struct Smem {
     static constexpr size_t seg_bytes = sizeof(float2) * L;                   // segment / exchange 1
     static constexpr size_t e2_bytes = sizeof(float2) * 16 * Geo<L>::LD2;    // exchange 2
-    static constexpr size_t total = 128 + seg_bytes + e2_bytes + 16;          // + alignment + mbarrier
+    static constexpr size_t h_bytes = sizeof(float2) * L;                     // one pre-transformed template
+    static constexpr size_t total = 128 + seg_bytes + e2_bytes + 2 * h_bytes + 3 * 8;
 };
 
 template <int L, int MINB>
@@ -35,11 +36,13 @@ __global__ void __launch_bounds__(L / 16, MINB)
     using Gm = Geo<L>;
     constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
     constexpr int MASK = L - 1;
+    constexpr uint32_t HBYTES = (uint32_t)Smem<L>::h_bytes;
 
     extern __shared__ unsigned char smem_raw[];
     float2 *e1 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float2 *e2 = e1 + L;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(e2 + 16 * LD2);
+    float4 *hb = reinterpret_cast<float4 *>(e2 + 16 * LD2);    // [2][8][NT] template double buffer
+    uint64_t *bar = reinterpret_cast<uint64_t *>(hb + 2 * 8 * NT);   // [0] segment, [1..2] templates
 
     const int tid = threadIdx.x;
     const int seg = a.seg_begin + blockIdx.x;
@@ -49,15 +52,22 @@ __global__ void __launch_bounds__(L / 16, MINB)
     const int hi = tid >> 4;
 
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(bar, (uint32_t)(L * sizeof(float2)));
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)));
         const int c0 = seg * a.S - (a.K - 1);
 #pragma unroll
-        for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, bar);
+        for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, &bar[0]);
+        // the first two templates of this block's group
+        for (int i = 0; i < 2 && z0 + i < z1; ++i) {
+            mbar_arrive_expect_tx(&bar[1 + i], HBYTES);
+            bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, HBYTES, &bar[1 + i]);
+        }
     }
 
     // Inverse-transform twiddles, fixed for this thread across all templates.
@@ -75,9 +85,13 @@ __global__ void __launch_bounds__(L / 16, MINB)
         for (int b = 0; b < Q; ++b) tw2[g * Q + b] = cconj(__ldg(&a.tw[((b * R + cg) * k1) & MASK]));
     }
 
-    const bool ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
-    if (!ok) {
-        atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+    // Block-uniform decision: every thread leaves together if the segment never arrived.
+    if (!__syncthreads_and(mbar_wait_bounded(&bar[0], 0, kWaitLimitNs))) {
+        if (tid == 0) {
+            atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+            mbar_wait_bounded(&bar[1], 0, kWaitLimitNs);   // let in-flight copies land
+            mbar_wait_bounded(&bar[2], 0, kWaitLimitNs);
+        }
         return;
     }
 
@@ -123,15 +137,17 @@ __global__ void __launch_bounds__(L / 16, MINB)
 
     const int64_t seg_out = (int64_t)seg * a.S;                 // first output index of this segment
     const int64_t nvalid64 = a.n - seg_out;
-    const int nvalid = nvalid64 < a.S ? (int)nvalid64 : a.S;
-    const int km1 = a.K - 1;
+    const unsigned nvalid = (unsigned)(nvalid64 < a.S ? nvalid64 : a.S);
+    const int obase = tid - (a.K - 1);                          // output index of register slot 0
 
     for (int z = z0; z < z1; ++z) {
+        const int i = z - z0, buf = i & 1;
+        const float4 *hz = hb + buf * 8 * NT;
+        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], (i >> 1) & 1, kWaitLimitNs);
         // ---- element-wise product with H_z (1/L folded in)
-        const float4 *Hz = a.H + (size_t)z * 8 * NT;
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
-            const float4 h = __ldg(&Hz[jp * NT + tid]);
+            const float4 h = hz[jp * NT + tid];
             v[2 * jp] = cmul(X[2 * jp], make_float2(h.x, h.y));
             v[2 * jp + 1] = cmul(X[2 * jp + 1], make_float2(h.z, h.w));
         }
@@ -145,7 +161,18 @@ __global__ void __launch_bounds__(L / 16, MINB)
             for (int c = 0; c < R; ++c)
                 e1[k1 + 16 * k2 + 16 * Q * c] = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
         }
-        __syncthreads();
+        if (!__syncthreads_and(h_ok)) {      // template buffer never arrived: leave together
+            if (tid == 0) {
+                atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+                mbar_wait_bounded(&bar[2 - buf], ((i + 1) >> 1) & 1, kWaitLimitNs);
+            }
+            return;
+        }
+        // every thread has read hb[buf]: refill it with the template two ahead
+        if (tid == 0 && z + 2 < z1) {
+            mbar_arrive_expect_tx(&bar[1 + buf], HBYTES);
+            bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + 2) * 8 * NT, HBYTES, &bar[1 + buf]);
+        }
         // ---- inverse pass B': Q-point IDFT over k2, twiddle conj W_L^{(bR + c) k1}
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
@@ -166,12 +193,12 @@ __global__ void __launch_bounds__(L / 16, MINB)
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = e2[tid + LD2 * k];
         dft<16, 1>(v);
-        // ---- discard the first K-1 points, power, store
+        // ---- discard the first K-1 points, power, store the valid ones
         float *orow = a.out + (size_t)z * (size_t)a.n + seg_out;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int o = j * NT + tid - km1;
-            if (o >= 0 && o < nvalid) orow[o] = cabs2(v[j]);
+            const int o = j * NT + obase;
+            if ((unsigned)o < nvalid) orow[o] = cabs2(v[j]);
         }
     }
 }

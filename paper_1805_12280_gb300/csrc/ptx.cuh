@@ -77,6 +77,16 @@ __device__ __forceinline__ void tma_load_1d(void *dst_smem, const CUtensorMap *m
         : "memory");
 }
 
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16), completion on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Status bits written by kernels into the plan's device status word.
 enum : int { STATUS_WAIT_TIMEOUT = 1 };
 
