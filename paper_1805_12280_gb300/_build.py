@@ -55,9 +55,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     os.makedirs(OBJDIR, exist_ok=True)
 
+    extra = os.environ.get("FDAS_NVCC_EXTRA", "").split()   # e.g. -DFDAS_MINB_2048=2
+
     def compile_one(src: str) -> str:
         obj = os.path.join(OBJDIR, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

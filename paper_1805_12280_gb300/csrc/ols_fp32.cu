@@ -19,6 +19,17 @@
 #include "fft_regs.cuh"
 #include "ptx.cuh"
 
+// Minimum resident blocks per SM requested from the compiler (caps registers per thread).
+#ifndef FDAS_MINB_1024
+#define FDAS_MINB_1024 4
+#endif
+#ifndef FDAS_MINB_2048
+#define FDAS_MINB_2048 2
+#endif
+#ifndef FDAS_MINB_4096
+#define FDAS_MINB_4096 1
+#endif
+
 namespace fdas {
 
 template <int L>
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(L / 16, MINB)
 template <int L>
 static cudaError_t launch_l(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
 {
-    constexpr int MINB = (L == 4096) ? 1 : (L == 2048 ? 3 : 6);
+    constexpr int MINB = (L == 4096) ? FDAS_MINB_4096 : (L == 2048 ? FDAS_MINB_2048 : FDAS_MINB_1024);
     auto kern = ols_fp32_kernel<L, MINB>;
     const size_t smem = Smem<L>::total;
     static bool attr_set[64] = {};   // the attribute is per device
