@@ -49,7 +49,10 @@ typedef struct {
     int seg_len;      /* L, the overlap-save FFT length: 1024, 2048 or 4096 (0 = 2048) */
     int tpl_per_cta;  /* G, templates per thread block: 1..M (0 = all M) */
     int precision;    /* FDAS_PREC_* (0 = FP32) */
-    int autotune;     /* reserved for the batched form's tuner; 0 = off */
+    int autotune;     /* 1: time every (L in {1024, 2048, 4096}) x (G in {5, 17, 85}) with the
+                         persistent kernel on one array of min(n_max, 2^21) points and keep the
+                         fastest (seg_len is then ignored; a non-zero tpl_per_cta stays fixed);
+                         results are cached per process by (device, M, K, tuning length) */
 } fdas_opts;
 
 /* Read-only description of a plan. */
@@ -64,6 +67,8 @@ typedef struct {
     int     precision;    /* FDAS_PREC_* */
     int     device;       /* CUDA device ordinal the plan lives on */
     int64_t device_bytes; /* device memory owned by the plan */
+    int     tuned;        /* 1 if the autotuner chose seg_len and tpl_per_cta */
+    float   tune_ms[9];   /* autotuner: ms per plane of its tuning array, [L in 1024, 2048, 4096][G in 5, 17, 85] (0 = not run) */
 } fdas_plan_desc;
 
 /*
@@ -118,6 +123,26 @@ int fdas_convolve(fdas_plan p, const void *in_c64_dev, int64_t n, float *out_pow
  */
 int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *out_power_host,
                        void *stream);
+
+/*
+ * fdas_convolve_batch -- power planes of `count` arrays of uneven lengths in one
+ * persistent launch (the dedispersion trials of a beam share the templates).
+ *
+ *   ins[i]  : device pointer, complex64 [ns[i]], 16-byte aligned;  1 <= ns[i] <= n_max.
+ *   outs[i] : device pointer, float32 [M][ns[i]] row-major, 4-byte aligned.
+ *   The three arrays of pointers/lengths are host memory, read during the call.
+ *
+ * Enqueues, per group of up to 120 arrays, one replay of the plan's CUDA graph
+ * [reset the work counter -> persistent kernel with one block per resident slot]; the
+ * kernel's blocks take work items (array, template group, segment) from the counter.
+ * Items are identical to fdas_convolve's, so results equal those of fdas_convolve on
+ * each array.  Asynchronous.  Calls on one plan are serialised by the library on the
+ * host; their kernels run in stream order and must not overlap in time: do not
+ * issue batches of one plan on two streams that run concurrently.
+ * Errors: INVALID_ARG (any entry invalid: nothing is enqueued), CUDA.
+ */
+int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns,
+                        float *const *outs, void *stream);
 
 /*
  * fdas_plan_status -- wait for `stream`, then read and clear the plan's device

@@ -7,9 +7,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 
 #include "fdas_internal.cuh"
 
@@ -100,6 +102,18 @@ struct fdas_plan_s {
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
     int *d_status = nullptr;
     int64_t device_bytes = 0;
+    // batched form: work counter, graph [memset counter -> persistent kernel], host table
+    int *d_counter = nullptr;
+    std::mutex batch_mu;
+    fdas::BatchKernel bk;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphNode_t kernel_node = nullptr;
+    fdas::BatchTable *table = nullptr;      // host copy, 64-byte aligned
+    fdas::OlsArgs batch_args = {};
+    // autotuner results, ms per plane of the tuning array, [L index][G index]
+    float tune_ms[3][3] = {};
+    int tuned = 0;
     // host-buffer entry point
     std::mutex host_mu;
     void *d_in_stage = nullptr;
@@ -120,6 +134,10 @@ void plan_free(fdas_plan p)
     cudaFree(p->d_status);
     cudaFree(p->d_in_stage);
     cudaFree(p->d_out_stage);
+    cudaFree(p->d_counter);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->table) ::operator delete(p->table, std::align_val_t(64));
     for (auto &e : p->chunk_ev)
         if (e) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
@@ -157,6 +175,233 @@ int enqueue_segments(fdas_plan p, const CUtensorMap *map, int64_t n, float *out,
     a.status = p->d_status;
     cudaError_t e = fdas::launch_ols_fp32(p->L, map, a, (int)(s1 - s0), stream);
     if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch");
+    return FDAS_OK;
+}
+
+
+// (Re)build the FP64 twiddles and the pre-transformed templates for segment length L.
+int build_templates(fdas_plan p, const float2 *d_h32, int L)
+{
+    cudaFree(p->d_tw);
+    cudaFree(p->d_tw64);
+    cudaFree(p->d_H);
+    p->d_tw = nullptr;
+    p->d_tw64 = nullptr;
+    p->d_H = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_tw, sizeof(float2) * L)) != cudaSuccess) return cuda_fail(e, "cudaMalloc twiddles");
+    if ((e = cudaMalloc(&p->d_tw64, sizeof(double2) * L)) != cudaSuccess) return cuda_fail(e, "cudaMalloc twiddles64");
+    if ((e = cudaMalloc(&p->d_H, sizeof(float4) * (size_t)p->M * 8 * (L / 16))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc templates");
+    if ((e = fdas::launch_twiddles(L, p->d_tw64, p->d_tw, nullptr)) != cudaSuccess) return cuda_fail(e, "twiddle kernel");
+    if ((e = fdas::launch_pretransform(L, d_h32, p->M, p->K_user, p->d_tw64, p->d_H, nullptr)) != cudaSuccess)
+        return cuda_fail(e, "pretransform kernel");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan-time kernels");
+    p->L = L;
+    p->S = (L - p->K + 1) & ~3;
+    p->bk = fdas::BatchKernel();
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        cudaGraphDestroy(p->graph);
+        p->graph_exec = nullptr;
+        p->graph = nullptr;
+    }
+    if ((e = fdas::batch_kernel(L, &p->bk)) != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
+    return FDAS_OK;
+}
+
+// Build the batch graph once: [memset work counter] -> [persistent kernel over all resident blocks].
+int ensure_graph(fdas_plan p)
+{
+    if (p->graph_exec) return FDAS_OK;
+    if (!p->table) {
+        p->table = static_cast<fdas::BatchTable *>(::operator new(sizeof(fdas::BatchTable), std::align_val_t(64)));
+        std::memset(p->table, 0, sizeof(fdas::BatchTable));
+    }
+    cudaError_t e;
+    if ((e = cudaGraphCreate(&p->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph create");
+    cudaMemsetParams mp = {};
+    mp.dst = p->d_counter;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 1;
+    mp.height = 1;
+    cudaGraphNode_t ms;
+    if ((e = cudaGraphAddMemsetNode(&ms, p->graph, nullptr, 0, &mp)) != cudaSuccess) return cuda_fail(e, "graph memset node");
+    void *args[3] = {p->table, &p->batch_args, &p->d_counter};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void *>(p->bk.fn);
+    kp.gridDim = dim3(p->bk.resident);
+    kp.blockDim = dim3(p->bk.block);
+    kp.sharedMemBytes = (unsigned)p->bk.smem;
+    kp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&p->kernel_node, p->graph, &ms, 1, &kp)) != cudaSuccess)
+        return cuda_fail(e, "graph kernel node");
+    if ((e = cudaGraphInstantiate(&p->graph_exec, p->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    return FDAS_OK;
+}
+
+int validate_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs)
+{
+    if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");
+    if (count < 0 || (count > 0 && (!ins || !ns || !outs))) return fail(FDAS_ERR_INVALID_ARG, "bad batch arrays");
+    for (int i = 0; i < count; ++i) {
+        int rc = validate_convolve(p, ins[i], ns[i], outs[i]);
+        if (rc) return fail(rc, "batch entry %d: %s", i, g_last_error.c_str());
+    }
+    return FDAS_OK;
+}
+
+// Fill the table for arrays [first, first + cnt) and replay the graph on `stream`.
+int enqueue_batch_chunk(fdas_plan p, int first, int cnt, const void *const *ins, const int64_t *ns,
+                        float *const *outs, cudaStream_t stream)
+{
+    fdas::BatchTable &t = *p->table;
+    const int ngroups = (p->M + p->G - 1) / p->G;
+    int64_t items = 0;
+    for (int i = 0; i < cnt; ++i) {
+        fdas::BatchArray &a = t.arr[i];
+        int rc = encode_input_map(&a.map, ins[first + i], ns[first + i]);
+        if (rc) return rc;
+        a.out = outs[first + i];
+        a.n = ns[first + i];
+        a.nseg = (int)n_segments(p, a.n);
+        a.item_off = items;
+        items += (int64_t)a.nseg * ngroups;
+    }
+    t.count = cnt;
+    t.total_items = items;
+    fdas::OlsArgs &a = p->batch_args;
+    a.H = p->d_H;
+    a.tw = p->d_tw;
+    a.out = nullptr;
+    a.n = 0;
+    a.M = p->M;
+    a.G = p->G;
+    a.S = p->S;
+    a.K = p->K;
+    a.seg_begin = 0;
+    a.status = p->d_status;
+    void *args[3] = {p->table, &p->batch_args, &p->d_counter};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void *>(p->bk.fn);
+    kp.gridDim = dim3(p->bk.resident);
+    kp.blockDim = dim3(p->bk.block);
+    kp.sharedMemBytes = (unsigned)p->bk.smem;
+    kp.kernelParams = args;
+    cudaError_t e;
+    if ((e = cudaGraphExecKernelNodeSetParams(p->graph_exec, p->kernel_node, &kp)) != cudaSuccess)
+        return cuda_fail(e, "graph kernel params");
+    if ((e = cudaGraphLaunch(p->graph_exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    return FDAS_OK;
+}
+
+int enqueue_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs,
+                  cudaStream_t stream)
+{
+    int rc = ensure_graph(p);
+    if (rc) return rc;
+    for (int first = 0; first < count; first += fdas::kBatchMax) {
+        const int cnt = std::min(fdas::kBatchMax, count - first);
+        if ((rc = enqueue_batch_chunk(p, first, cnt, ins, ns, outs, stream))) return rc;
+    }
+    return FDAS_OK;
+}
+
+// Autotuner: time the persistent kernel for every (L, G) candidate on one array of
+// min(n_max, 2^21) points and keep the fastest; results are cached per process by
+// (device, M, K, tuning length).
+struct TuneKey {
+    int dev, M, K;
+    int64_t n;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(dev, M, K, n) < std::tie(o.dev, o.M, o.K, o.n);
+    }
+};
+struct TuneVal {
+    int L, G;
+    float ms[3][3];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+const int kTuneL[3] = {1024, 2048, 4096};
+const int kTuneG[3] = {5, 17, 85};
+
+int autotune(fdas_plan p, const float2 *d_h32, int fixed_G)
+{
+    const int64_t n = std::min<int64_t>(p->n_max, int64_t(1) << 21);
+    const TuneKey key{p->device, p->M, p->K_user, n};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && !fixed_G) {
+            p->L = it->second.L;
+            p->G = it->second.G;
+            std::memcpy(p->tune_ms, it->second.ms, sizeof p->tune_ms);
+            p->tuned = 1;
+            return FDAS_OK;
+        }
+    }
+    void *d_in = nullptr;
+    float *d_out = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_in, sizeof(float2) * n)) != cudaSuccess) return cuda_fail(e, "autotune input");
+    if ((e = cudaMalloc(&d_out, sizeof(float) * n * p->M)) != cudaSuccess) {
+        cudaFree(d_in);
+        return cuda_fail(e, "autotune output");
+    }
+    cudaMemset(d_in, 0x3c, sizeof(float2) * n);   // finite, non-denormal values
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bestL = p->L, bestG = p->G, rc = FDAS_OK;
+    const void *ins[1] = {d_in};
+    const int64_t ns[1] = {n};
+    float *outs[1] = {d_out};
+    for (int li = 0; li < 3 && rc == FDAS_OK; ++li) {
+        const int L = kTuneL[li];
+        if (p->K > L - 4) continue;
+        if ((rc = build_templates(p, d_h32, L))) break;
+        for (int gi = 0; gi < 3 && rc == FDAS_OK; ++gi) {
+            const int G = fixed_G ? fixed_G : std::min(kTuneG[gi], p->M);
+            p->G = G;
+            float ms = 0.f;
+            for (int rep = 0; rep < 4 && rc == FDAS_OK; ++rep) {
+                cudaEventRecord(e0, nullptr);
+                rc = enqueue_batch(p, 1, ins, ns, outs, nullptr);
+                cudaEventRecord(e1, nullptr);
+                if (rc == FDAS_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune run");
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t / 3.f;
+            }
+            p->tune_ms[li][gi] = ms;
+            if (rc == FDAS_OK && ms < best) {
+                best = ms;
+                bestL = L;
+                bestG = G;
+            }
+            if (fixed_G) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_in);
+    cudaFree(d_out);
+    if (rc != FDAS_OK) return rc;
+    if ((rc = fdas_plan_status(p, nullptr)) != FDAS_OK) return rc;
+    p->L = bestL;
+    p->G = bestG;
+    p->tuned = 1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!fixed_G) {
+        TuneVal v{bestL, bestG, {}};
+        std::memcpy(v.ms, p->tune_ms, sizeof v.ms);
+        g_tune_cache[key] = v;
+    }
     return FDAS_OK;
 }
 
@@ -217,27 +462,25 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
         plan_free(p);
         return code;
     };
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc status"));
+    if ((e = cudaMalloc(&p->d_counter, 256)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc work counter"));
+    if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup_fail(cuda_fail(e, "memset status"));
+    if ((e = cudaMemset(p->d_counter, 0, 256)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "memset counter"));
     float2 *d_h32 = nullptr;
     const size_t h_bytes = sizeof(float2) * (size_t)M * K;
-    const size_t H_bytes = sizeof(float4) * (size_t)M * 8 * (L / 16);
-    cudaError_t e;
-    if ((e = cudaMalloc(&p->d_tw, sizeof(float2) * L)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc twiddles"));
-    if ((e = cudaMalloc(&p->d_tw64, sizeof(double2) * L)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc twiddles64"));
-    if ((e = cudaMalloc(&p->d_H, H_bytes)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc templates"));
-    if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc status"));
     if ((e = cudaMalloc(&d_h32, h_bytes)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc template staging"));
-    p->device_bytes = (int64_t)(sizeof(float2) * L + sizeof(double2) * L + H_bytes + sizeof(int));
-
-    cudaStream_t s = nullptr;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_h32, templates, h_bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = fdas::launch_twiddles(L, p->d_tw64, p->d_tw, s);
-    if (e == cudaSuccess) e = fdas::launch_pretransform(L, d_h32, M, K, p->d_tw64, p->d_H, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (s) cudaStreamDestroy(s);
+    if ((e = cudaMemcpy(d_h32, templates, h_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(d_h32);
+        return cleanup_fail(cuda_fail(e, "copy templates"));
+    }
+    int rc = FDAS_OK;
+    if (o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
+    if (rc == FDAS_OK) rc = build_templates(p, d_h32, p->L);
     cudaFree(d_h32);
-    if (e != cudaSuccess) return cleanup_fail(cuda_fail(e, "plan-time kernels"));
+    if (rc != FDAS_OK) return cleanup_fail(rc);
+    p->device_bytes = (int64_t)(sizeof(float2) * p->L + sizeof(double2) * p->L +
+                                sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) + 256);
     *out = p;
     return FDAS_OK;
 }
@@ -255,7 +498,21 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *d)
     d->precision = p->precision;
     d->device = p->device;
     d->device_bytes = p->device_bytes;
+    d->tuned = p->tuned;
+    for (int i = 0; i < 9; ++i) d->tune_ms[i] = p->tune_ms[i / 3][i % 3];
     return FDAS_OK;
+}
+
+int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs,
+                        void *stream)
+{
+    int rc = validate_batch(p, count, ins, ns, outs);
+    if (rc) return rc;
+    if (count == 0) return FDAS_OK;
+    std::lock_guard<std::mutex> lk(p->batch_mu);
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(FDAS_ERR_CUDA, "cannot select plan device %d", p->device);
+    return enqueue_batch(p, count, ins, ns, outs, (cudaStream_t)stream);
 }
 
 int fdas_convolve(fdas_plan p, const void *in, int64_t n, float *out, void *stream)

@@ -53,6 +53,32 @@ struct OlsArgs {
     int *status;          // device status word (bit 0: a bounded wait ran out)
 };
 
+// One array of a batch: its input tensor map (param space), output plane and work items.
+struct alignas(64) BatchArray {
+    CUtensorMap map;      // 1-D tiled map over the array's complex64 input
+    float *out;           // [M][n]
+    int64_t n;
+    int64_t item_off;     // index of the array's first work item
+    int nseg;             // segments of this array
+    int pad_;
+};
+constexpr int kBatchMax = 120;   // arrays per launch: the table is a kernel parameter (< 32 KB)
+struct alignas(64) BatchTable {
+    int count;
+    int pad_;
+    int64_t total_items;
+    BatchArray arr[kBatchMax];
+};
+
+// Resolved persistent batch kernel for one segment length.
+struct BatchKernel {
+    const void *fn = nullptr;
+    int block = 0;
+    size_t smem = 0;
+    int resident = 0;     // blocks that fit on the device at once
+};
+cudaError_t batch_kernel(int L, BatchKernel *k);
+
 // Launch the FP32 segment kernel over segments [seg_begin, seg_begin + nseg).
 cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, int nseg,
                             cudaStream_t s);

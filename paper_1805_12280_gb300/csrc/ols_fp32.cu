@@ -1,17 +1,19 @@
-// Fused FP32 overlap-save segment kernel (Algorithm 2 with the forward FFT shared by
+// Fused FP32 overlap-save segment kernels (Algorithm 2 with the forward FFT shared by
 // all templates, Table 1 text; power output, Sec. 4.3).
 //
-// One thread block of NT = L/16 threads owns one input segment and a group of G
-// templates:
+// One work item = (array, segment, template group).  A block of NT = L/16 threads:
 //   1. TMA loads the L-point segment x[s*S - (K-1) .. s*S - (K-1) + L) into shared
 //      memory; the tensor map zero-fills before 0 (the K-1 leading zeros of the first
 //      segment) and past n;
 //   2. forward FFT (passes A, B, C; two shared-memory exchanges), the spectrum stays
 //      in registers for the whole template loop;
-//   3. per template: element-wise product with the pre-transformed template (read
-//      from L2, layout matched to the register distribution), inverse FFT (passes
-//      C', B', A'; two exchanges; 1/L is folded into the template), discard of the
-//      first K-1 points, |y|^2, coalesced stores of the valid S points.
+//   3. per template: element-wise product with the pre-transformed template (prefetched
+//      two templates ahead into a shared-memory double buffer by cp.async.bulk), inverse
+//      FFT (passes C', B', A'; two exchanges; 1/L is folded into the template), discard
+//      of the first K-1 points, |y|^2, coalesced stores of the valid S points.
+// ols_fp32_kernel runs one item per block (grid = segments x groups of one array);
+// ols_fp32_batch is persistent: resident blocks pull items of many arrays from a
+// device work counter.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -40,49 +42,43 @@ struct Smem {
     static constexpr size_t total = 128 + seg_bytes + e2_bytes + 2 * h_bytes + 3 * 8;
 };
 
-template <int L, int MINB>
-__global__ void __launch_bounds__(L / 16, MINB)
-    ols_fp32_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a)
+template <int L>
+constexpr int minb()
+{
+    return L == 4096 ? FDAS_MINB_4096 : (L == 2048 ? FDAS_MINB_2048 : FDAS_MINB_1024);
+}
+
+// Shared-memory carve-up and mbarrier phase bookkeeping of one block.
+template <int L>
+struct Block {
+    float2 *e1;      // segment, then exchange buffer 1 [L]
+    float2 *e2;      // exchange buffer 2 [16][NT + 1]
+    float4 *hb;      // template double buffer [2][8][NT]
+    uint64_t *bar;   // [0] segment, [1], [2] template buffers
+    uint32_t seg_uses = 0, h_uses[2] = {0, 0};   // completed phases per barrier
+
+    __device__ explicit Block(unsigned char *raw)
+    {
+        e1 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+        e2 = e1 + L;
+        hb = reinterpret_cast<float4 *>(e2 + 16 * Geo<L>::LD2);
+        bar = reinterpret_cast<uint64_t *>(hb + 2 * 8 * Geo<L>::NT);
+    }
+};
+
+template <int L>
+__device__ __forceinline__ void init_block(Block<L> &B, const OlsArgs &a, float2 (&tw1)[16], float2 (&tw2)[16])
 {
     using Gm = Geo<L>;
-    constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
-    constexpr int MASK = L - 1;
-    constexpr uint32_t HBYTES = (uint32_t)Smem<L>::h_bytes;
-
-    extern __shared__ unsigned char smem_raw[];
-    float2 *e1 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float2 *e2 = e1 + L;
-    float4 *hb = reinterpret_cast<float4 *>(e2 + 16 * LD2);    // [2][8][NT] template double buffer
-    uint64_t *bar = reinterpret_cast<uint64_t *>(hb + 2 * 8 * NT);   // [0] segment, [1..2] templates
-
-    const int tid = threadIdx.x;
-    const int seg = a.seg_begin + blockIdx.x;
-    const int z0 = blockIdx.y * a.G;
-    const int z1 = min(z0 + a.G, a.M);
-    const int k1 = tid & 15;
-    const int hi = tid >> 4;
-
+    constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, MASK = L - 1;
+    const int tid = threadIdx.x, k1 = tid & 15, hi = tid >> 4;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], 1);
+        mbar_init(&B.bar[0], 1);
+        mbar_init(&B.bar[1], 1);
+        mbar_init(&B.bar[2], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)));
-        const int c0 = seg * a.S - (a.K - 1);
-#pragma unroll
-        for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, &bar[0]);
-        // the first two templates of this block's group
-        for (int i = 0; i < 2 && z0 + i < z1; ++i) {
-            mbar_arrive_expect_tx(&bar[1 + i], HBYTES);
-            bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, HBYTES, &bar[1 + i]);
-        }
-    }
-
-    // Inverse-transform twiddles, fixed for this thread across all templates.
-    float2 tw1[16], tw2[16];
+    // Inverse-transform twiddles, fixed for this thread across all items and templates.
 #pragma unroll
     for (int g = 0; g < GC; ++g) {
         const int k2 = hi + (NT / 16) * g;
@@ -95,15 +91,57 @@ __global__ void __launch_bounds__(L / 16, MINB)
 #pragma unroll
         for (int b = 0; b < Q; ++b) tw2[g * Q + b] = cconj(__ldg(&a.tw[((b * R + cg) * k1) & MASK]));
     }
+    __syncthreads();
+}
 
+// After a timed-out wait: give each copy that may still be in flight a bounded time to
+// land before the block exits.  `pending` bit i: barrier i has an issued, un-awaited phase
+// whose parity is `parity` bit i.
+__device__ __noinline__ void drain(uint64_t *bar, unsigned pending, unsigned parity)
+{
+    for (int i = 0; i < 3; ++i)
+        if (pending & (1u << i)) mbar_wait_bounded(&bar[i], (parity >> i) & 1u, kWaitLimitNs);
+}
+
+// One work item.  Every thread of the block calls it with the same arguments after a
+// block-wide barrier that follows the previous item.  Returns false (block-uniformly)
+// if a bounded wait ran out; the status bit is then set.
+template <int L>
+__device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CUtensorMap *map, int seg, int z0,
+                                         int z1, int64_t n, float *out, const float2 (&tw1)[16],
+                                         const float2 (&tw2)[16])
+{
+    using Gm = Geo<L>;
+    constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
+    constexpr int MASK = L - 1;
+    constexpr uint32_t HBYTES = (uint32_t)Smem<L>::h_bytes;
+    float2 *e1 = B.e1, *e2 = B.e2;
+    float4 *hb = B.hb;
+    uint64_t *bar = B.bar;
+    const int tid = threadIdx.x, k1 = tid & 15, hi = tid >> 4;
+
+    if (tid == 0) {
+        fence_proxy_async_smem();   // earlier generic writes to e1/hb are ordered before the async copies
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)));
+        const int c0 = seg * a.S - (a.K - 1);
+#pragma unroll
+        for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, map, c0 + 256 * j, &bar[0]);
+        for (int i = 0; i < 2 && z0 + i < z1; ++i) {
+            mbar_arrive_expect_tx(&bar[1 + i], HBYTES);
+            bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, HBYTES, &bar[1 + i]);
+        }
+    }
     // Block-uniform decision: every thread leaves together if the segment never arrived.
-    if (!__syncthreads_and(mbar_wait_bounded(&bar[0], 0, kWaitLimitNs))) {
+    const bool seg_ok = mbar_wait_bounded(&bar[0], B.seg_uses & 1, kWaitLimitNs);
+    B.seg_uses++;
+    if (!__syncthreads_and(seg_ok)) {
         if (tid == 0) {
             atomicOr(a.status, STATUS_WAIT_TIMEOUT);
-            mbar_wait_bounded(&bar[1], 0, kWaitLimitNs);   // let in-flight copies land
-            mbar_wait_bounded(&bar[2], 0, kWaitLimitNs);
+            const unsigned pending = 1u | 2u | (z0 + 1 < z1 ? 4u : 0u);
+            const unsigned parity = ((B.seg_uses - 1) & 1u) | ((B.h_uses[0] & 1u) << 1) | ((B.h_uses[1] & 1u) << 2);
+            drain(bar, pending, parity);
         }
-        return;
+        return false;
     }
 
     float2 v[16], X[16];
@@ -147,14 +185,15 @@ __global__ void __launch_bounds__(L / 16, MINB)
     __syncthreads();   // every thread has read e1 before the template loop rewrites it
 
     const int64_t seg_out = (int64_t)seg * a.S;                 // first output index of this segment
-    const int64_t nvalid64 = a.n - seg_out;
+    const int64_t nvalid64 = n - seg_out;
     const unsigned nvalid = (unsigned)(nvalid64 < a.S ? nvalid64 : a.S);
     const int obase = tid - (a.K - 1);                          // output index of register slot 0
 
     for (int z = z0; z < z1; ++z) {
-        const int i = z - z0, buf = i & 1;
+        const int buf = (z - z0) & 1;
         const float4 *hz = hb + buf * 8 * NT;
-        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], (i >> 1) & 1, kWaitLimitNs);
+        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], B.h_uses[buf] & 1, kWaitLimitNs);
+        B.h_uses[buf]++;
         // ---- element-wise product with H_z (1/L folded in)
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
@@ -172,12 +211,15 @@ __global__ void __launch_bounds__(L / 16, MINB)
             for (int c = 0; c < R; ++c)
                 e1[k1 + 16 * k2 + 16 * Q * c] = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
         }
-        if (!__syncthreads_and(h_ok)) {      // template buffer never arrived: leave together
+        if (!__syncthreads_and(h_ok)) {      // a template buffer never arrived: leave together
             if (tid == 0) {
                 atomicOr(a.status, STATUS_WAIT_TIMEOUT);
-                mbar_wait_bounded(&bar[2 - buf], ((i + 1) >> 1) & 1, kWaitLimitNs);
+                const int other = 1 - buf;
+                const unsigned pending = (2u << buf) | (z + 1 < z1 ? (2u << other) : 0u);
+                const unsigned parity = (((B.h_uses[buf] - 1) & 1u) << (1 + buf)) | ((B.h_uses[other] & 1u) << (1 + other));
+                drain(bar, pending, parity);
             }
-            return;
+            return false;
         }
         // every thread has read hb[buf]: refill it with the template two ahead
         if (tid == 0 && z + 2 < z1) {
@@ -205,32 +247,81 @@ __global__ void __launch_bounds__(L / 16, MINB)
         for (int k = 0; k < 16; ++k) v[k] = e2[tid + LD2 * k];
         dft<16, 1>(v);
         // ---- discard the first K-1 points, power, store the valid ones
-        float *orow = a.out + (size_t)z * (size_t)a.n + seg_out;
+        float *orow = out + (size_t)z * (size_t)n + seg_out;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int o = j * NT + obase;
             if ((unsigned)o < nvalid) orow[o] = cabs2(v[j]);
         }
     }
+    return true;
+}
+
+// One item per block: blockIdx.x = segment (from a.seg_begin), blockIdx.y = template group.
+template <int L, int MINB>
+__global__ void __launch_bounds__(L / 16, MINB)
+    ols_fp32_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Block<L> B(smem_raw);
+    float2 tw1[16], tw2[16];
+    init_block<L>(B, a, tw1, tw2);
+    const int z0 = blockIdx.y * a.G;
+    run_item<L>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out, tw1, tw2);
+}
+
+// Persistent: resident blocks take items (array, group, segment) from *counter until the
+// table is exhausted.  Items are numbered array by array, group-major inside an array, so
+// concurrently running blocks share templates and neighbouring segments in L2.
+template <int L, int MINB>
+__global__ void __launch_bounds__(L / 16, MINB)
+    ols_fp32_batch(const __grid_constant__ BatchTable tab, const OlsArgs a, int *counter)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int item_sh;
+    Block<L> B(smem_raw);
+    float2 tw1[16], tw2[16];
+    init_block<L>(B, a, tw1, tw2);
+    for (;;) {
+        __syncthreads();                       // the previous item is finished by every thread
+        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t item = item_sh;
+        if (item >= tab.total_items) break;
+        int lo = 0, hi = tab.count - 1;        // last array whose first item <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab.arr[mid].item_off <= item) lo = mid; else hi = mid - 1;
+        }
+        const BatchArray &ar = tab.arr[lo];
+        const int64_t local = item - ar.item_off;
+        const int g = (int)(local / ar.nseg), seg = (int)(local % ar.nseg);
+        const int z0 = g * a.G;
+        if (!run_item<L>(B, a, &ar.map, seg, z0, min(z0 + a.G, a.M), ar.n, ar.out, tw1, tw2)) return;
+    }
+}
+
+template <int L>
+static cudaError_t set_smem_attr(const void *fn, bool *done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<L>::total);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
 }
 
 template <int L>
 static cudaError_t launch_l(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
 {
-    constexpr int MINB = (L == 4096) ? FDAS_MINB_4096 : (L == 2048 ? FDAS_MINB_2048 : FDAS_MINB_1024);
-    auto kern = ols_fp32_kernel<L, MINB>;
-    const size_t smem = Smem<L>::total;
-    static bool attr_set[64] = {};   // the attribute is per device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    auto kern = ols_fp32_kernel<L, minb<L>()>;
+    static bool done[64] = {};
+    cudaError_t e = set_smem_attr<L>((const void *)kern, done);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
-    }
     dim3 grid(nseg, (a.M + a.G - 1) / a.G);
-    kern<<<grid, L / 16, smem, s>>>(*tmap, a);
+    kern<<<grid, L / 16, Smem<L>::total, s>>>(*tmap, a);
     return cudaGetLastError();
 }
 
@@ -240,6 +331,35 @@ cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, in
     case 1024: return launch_l<1024>(tmap, a, nseg, s);
     case 2048: return launch_l<2048>(tmap, a, nseg, s);
     case 4096: return launch_l<4096>(tmap, a, nseg, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int L>
+static cudaError_t batch_kernel_l(BatchKernel *k)
+{
+    auto kern = ols_fp32_batch<L, minb<L>()>;
+    static bool done[64] = {};
+    cudaError_t e = set_smem_attr<L>((const void *)kern, done);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L / 16, Smem<L>::total)) != cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    k->fn = (const void *)kern;
+    k->block = L / 16;
+    k->smem = Smem<L>::total;
+    k->resident = per_sm * sms;
+    return cudaSuccess;
+}
+
+cudaError_t batch_kernel(int L, BatchKernel *k)
+{
+    switch (L) {
+    case 1024: return batch_kernel_l<1024>(k);
+    case 2048: return batch_kernel_l<2048>(k);
+    case 4096: return batch_kernel_l<4096>(k);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -43,7 +43,7 @@ class fdas_plan_desc(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("n_templates", ctypes.c_int), ("tpl_len", ctypes.c_int),
                 ("frame_len", ctypes.c_int), ("seg_len", ctypes.c_int), ("seg_step", ctypes.c_int),
                 ("tpl_per_cta", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9)]
 
 
 # Every exported symbol with (restype, argtypes).  The CPU tests check that the
@@ -56,6 +56,7 @@ SIGNATURES = {
     "fdas_plan_describe": (_I, [_P, ctypes.POINTER(fdas_plan_desc)]),
     "fdas_convolve": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_host": (_I, [_P, _P, _I64, _P, _P]),
+    "fdas_convolve_batch": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_plan_status": (_I, [_P, _P]),
     "fdas_destroy": (_I, [_P]),
     "fdas_strerror": (ctypes.c_char_p, [_I]),
@@ -120,6 +121,16 @@ def fdas_convolve_host(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int
     _check(load().fdas_convolve_host(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_convolve_host")
 
 
+def fdas_convolve_batch(plan: int, in_ptrs, ns, out_ptrs, stream: int = 0) -> None:
+    count = len(in_ptrs)
+    if len(ns) != count or len(out_ptrs) != count:
+        raise ValueError("in_ptrs, ns and out_ptrs must have the same length")
+    ins = (_P * max(count, 1))(*[_P(int(v)) for v in in_ptrs])
+    nn = (_I64 * max(count, 1))(*[int(v) for v in ns])
+    outs = (_P * max(count, 1))(*[_P(int(v)) for v in out_ptrs])
+    _check(load().fdas_convolve_batch(_P(plan), count, ins, nn, outs, _P(stream)), "fdas_convolve_batch")
+
+
 def fdas_plan_status(plan: int, stream: int = 0) -> None:
     _check(load().fdas_plan_status(_P(plan), _P(stream)), "fdas_plan_status")
 
@@ -167,6 +178,21 @@ class Plan:
             raise ValueError("out must be a contiguous float32 tensor with M*n elements")
         fdas_convolve(self.handle, x.data_ptr(), n, out.data_ptr(), _stream_handle(stream))
         return out
+
+    def convolve_batch(self, xs, outs=None, stream=None):
+        """Power planes of a list of device arrays in one persistent launch."""
+        import torch
+        for x in xs:
+            if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+                raise ValueError("every input must be a contiguous complex64 CUDA tensor")
+        if outs is None:
+            outs = [torch.empty((self.n_templates, x.numel()), dtype=torch.float32, device=x.device) for x in xs]
+        for x, o in zip(xs, outs):
+            if o.dtype != torch.float32 or not o.is_contiguous() or o.numel() != self.n_templates * x.numel():
+                raise ValueError("each output must be a contiguous float32 tensor with M*n elements")
+        fdas_convolve_batch(self.handle, [x.data_ptr() for x in xs], [x.numel() for x in xs],
+                            [o.data_ptr() for o in outs], _stream_handle(stream))
+        return outs
 
     def convolve_host(self, x: np.ndarray, out: np.ndarray | None = None, stream=0) -> np.ndarray:
         """Synchronous host-to-host form (host input, host plane)."""
