@@ -145,6 +145,33 @@ int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const in
                         float *const *outs, void *stream);
 
 /*
+ * fdas_convolve_batch_noalloc -- fdas_convolve_batch without any allocation in the call.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate GPU memory while they run, e.g. a real-time pipeline that must meet a
+ * per-trial deadline (cudaMalloc can take milliseconds and cudaFree synchronises the
+ * device), or a process whose device memory is owned up front by another allocator.
+ * It computes the same planes as fdas_convolve_batch (same arguments, same kernel,
+ * same work items) but allocates nothing: no cudaMalloc/cudaFree, no CUDA graph, no
+ * heap memory; the persistent kernel's work counters live in a fixed array of 64
+ * ints that the library places in every GPU's memory for the life of the process.
+ *
+ *   count <= 7680 (64 launches of up to 120 arrays); larger batches are rejected with
+ *   FDAS_ERR_INVALID_ARG and a message naming the limit.  Other arguments as for
+ *   fdas_convolve_batch.
+ *
+ * The first call on a device looks up the counter array's device address (once per
+ * device, with the plan's device current); make that first call before any stream
+ * capture.  Each call clears the counters it uses on `stream` before its launches.
+ * All calls in the process share the one array: calls whose work overlaps on the GPU
+ * (different streams, different plans, or different threads without ordering) race
+ * on it and must be serialised by the caller.  Asynchronous.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int fdas_convolve_batch_noalloc(fdas_plan p, int count, const void *const *ins, const int64_t *ns,
+                                float *const *outs, void *stream);
+
+/*
  * fdas_plan_status -- wait for `stream`, then read and clear the plan's device
  * status word.  Returns FDAS_OK, FDAS_ERR_TIMEOUT if an in-kernel bounded wait ran
  * out since the last call, or FDAS_ERR_CUDA if the stream reports an error.

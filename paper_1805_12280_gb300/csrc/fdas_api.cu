@@ -407,6 +407,63 @@ int autotune(fdas_plan p, const float2 *d_h32, int fixed_G)
 
 }  // namespace
 
+namespace fdas {
+
+// Direct (graph-free) launches of the persistent batch kernel, one per table of up to
+// kBatchMax arrays; launch c takes its work counter at counters[c].  The counters are
+// cleared on `stream` first.  Host memory used: the stack only; no device allocation.
+int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs,
+                 int *counters, int max_chunks, cudaStream_t stream)
+{
+    int rc = validate_batch(p, count, ins, ns, outs);
+    if (rc) return rc;
+    const int chunks = (count + kBatchMax - 1) / kBatchMax;
+    if (chunks > max_chunks)
+        return fail(FDAS_ERR_INVALID_ARG, "batch of %d arrays exceeds the %d-array limit of this entry point", count,
+                    max_chunks * kBatchMax);
+    if (count == 0) return FDAS_OK;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * chunks, stream)) != cudaSuccess)
+        return cuda_fail(e, "clear work counters");
+    alignas(64) BatchTable t;
+    OlsArgs a = {};
+    a.H = p->d_H;
+    a.tw = p->d_tw;
+    a.M = p->M;
+    a.G = p->G;
+    a.S = p->S;
+    a.K = p->K;
+    a.status = p->d_status;
+    const int ngroups = (p->M + p->G - 1) / p->G;
+    for (int c = 0; c < chunks; ++c) {
+        const int first = c * kBatchMax, cnt = std::min(kBatchMax, count - first);
+        int64_t items = 0;
+        for (int i = 0; i < cnt; ++i) {
+            BatchArray &ar = t.arr[i];
+            if ((rc = encode_input_map(&ar.map, ins[first + i], ns[first + i]))) return rc;
+            ar.out = outs[first + i];
+            ar.n = ns[first + i];
+            ar.nseg = (int)n_segments(p, ar.n);
+            ar.item_off = items;
+            items += (int64_t)ar.nseg * ngroups;
+        }
+        t.count = cnt;
+        t.total_items = items;
+        int *counter = counters + c;
+        void *args[3] = {&t, &a, &counter};
+        if ((e = cudaLaunchKernel(p->bk.fn, dim3(p->bk.resident), dim3(p->bk.block), args, p->bk.smem, stream)) !=
+            cudaSuccess)
+            return cuda_fail(e, "persistent batch kernel launch");
+    }
+    return FDAS_OK;
+}
+
+// Plan accessor and error reporting for code outside this file.
+int plan_device(fdas_plan p) { return p ? p->device : -1; }
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+}  // namespace fdas
+
 extern "C" {
 
 const char *fdas_version(void) { return "fdas-gb300 0.1 (sm_103a)"; }

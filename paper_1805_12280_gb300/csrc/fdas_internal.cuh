@@ -79,6 +79,13 @@ struct BatchKernel {
 };
 cudaError_t batch_kernel(int L, BatchKernel *k);
 
+// Graph-free launches of the persistent batch kernel with caller-provided work counters
+// (one per table of kBatchMax arrays, at most max_chunks); clears them on the stream first.
+int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs,
+                 int *counters, int max_chunks, cudaStream_t stream);
+int plan_device(fdas_plan p);
+int set_error(int code, const char *msg);   // records the thread-local message, returns code
+
 // Launch the FP32 segment kernel over segments [seg_begin, seg_begin + nseg).
 cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, int nseg,
                             cudaStream_t s);

@@ -57,6 +57,7 @@ SIGNATURES = {
     "fdas_convolve": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_host": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_batch": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
+    "fdas_convolve_batch_noalloc": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_plan_status": (_I, [_P, _P]),
     "fdas_destroy": (_I, [_P]),
     "fdas_strerror": (ctypes.c_char_p, [_I]),
@@ -129,6 +130,18 @@ def fdas_convolve_batch(plan: int, in_ptrs, ns, out_ptrs, stream: int = 0) -> No
     nn = (_I64 * max(count, 1))(*[int(v) for v in ns])
     outs = (_P * max(count, 1))(*[_P(int(v)) for v in out_ptrs])
     _check(load().fdas_convolve_batch(_P(plan), count, ins, nn, outs, _P(stream)), "fdas_convolve_batch")
+
+
+def fdas_convolve_batch_noalloc(plan: int, in_ptrs, ns, out_ptrs, stream: int = 0) -> None:
+    """Same as fdas_convolve_batch, for callers that cannot allocate GPU memory at call time."""
+    count = len(in_ptrs)
+    if len(ns) != count or len(out_ptrs) != count:
+        raise ValueError("in_ptrs, ns and out_ptrs must have the same length")
+    ins = (_P * max(count, 1))(*[_P(int(v)) for v in in_ptrs])
+    nn = (_I64 * max(count, 1))(*[int(v) for v in ns])
+    outs = (_P * max(count, 1))(*[_P(int(v)) for v in out_ptrs])
+    _check(load().fdas_convolve_batch_noalloc(_P(plan), count, ins, nn, outs, _P(stream)),
+           "fdas_convolve_batch_noalloc")
 
 
 def fdas_plan_status(plan: int, stream: int = 0) -> None:
