@@ -178,6 +178,64 @@ int fdas_convolve_batch_noalloc(fdas_plan p, int count, const void *const *ins, 
  */
 int fdas_plan_status(fdas_plan p, void *stream);
 
+/* ------------------------------------------------------------------------------------
+ * Served form: continuous batching over one plan.
+ *
+ * Requests (device input arrays) are admitted in arrival order as soon as the memory
+ * for their planes (4*M*n bytes, rounded up to 256) is free in a pool reserved once at
+ * creation; admitted requests are packed into batches of up to max_batch arrays and
+ * launched on whichever of the `lanes` streams is idle, so a request that arrives while
+ * others run on the GPU starts as soon as a lane and memory free up, and batches on
+ * different lanes overlap on the device.  The plan (templates, transforms, kernels)
+ * stays resident; the plan must outlive the server.  A request's plane stays in the
+ * pool until fdas_server_release.  Each request's plane equals fdas_convolve's for the
+ * same input (same kernel, same work items).
+ * ---------------------------------------------------------------------------------- */
+typedef struct fdas_server_s *fdas_server;
+
+typedef struct {
+    int64_t budget_bytes;  /* device memory for output planes, reserved at creation (> 0) */
+    int     lanes;         /* concurrent batch streams, 1..16 (0 = 2) */
+    int     max_batch;     /* arrays per launch, 1..120 (0 = 32) */
+} fdas_server_opts;
+
+typedef struct {
+    int64_t submitted, completed, rejected;
+    int64_t queued;            /* waiting for plane memory */
+    int64_t in_flight;         /* admitted and not yet released */
+    int64_t bytes_in_use, peak_bytes_in_use;
+    int64_t admission_waits;   /* requests that could not be admitted when submitted */
+    int64_t launches;          /* batch launches */
+    double  p50_ms, p99_ms, mean_ms, max_ms;   /* latency: submit -> plane complete on the GPU */
+    double  arrays_per_s;      /* completed / (last completion - first submission) */
+} fdas_server_report;
+
+/* Create a server (starts its scheduler thread; reserves budget_bytes on the plan's
+ * device).  Errors: INVALID_ARG, OOM, CUDA. */
+int fdas_server_create(fdas_server *out, fdas_plan plan, const fdas_server_opts *opts);
+
+/* Queue one request.  in_c64_dev: device complex64 [n], 16-byte aligned, valid until
+ * the request completes; 1 <= n <= n_max.  Non-blocking.  *ticket identifies it.
+ * Errors: INVALID_ARG, REJECTED (its plane alone exceeds the budget). */
+int fdas_server_submit(fdas_server s, const void *in_c64_dev, int64_t n, int64_t *ticket);
+
+/* Wait until the request's plane is complete (timeout_ms < 0: no limit); *plane_dev
+ * (optional) receives its device address, float32 [M][n].  Errors: INVALID_ARG
+ * (unknown ticket), TIMEOUT, CUDA (the launch failed). */
+int fdas_server_wait(fdas_server s, int64_t ticket, int64_t timeout_ms, float **plane_dev);
+
+/* Return a completed request's plane memory to the pool.  Errors: INVALID_ARG, BUSY
+ * (still queued or running). */
+int fdas_server_release(fdas_server s, int64_t ticket);
+
+/* Counters and latency percentiles since creation or the last reset. */
+int fdas_server_stats(fdas_server s, fdas_server_report *report);
+int fdas_server_reset_stats(fdas_server s);
+
+/* Stop the scheduler, let launched batches finish, free the pool and the lanes;
+ * planes not yet launched are dropped. */
+int fdas_server_destroy(fdas_server s);
+
 /* Free the plan.  The caller must have synchronised every stream that used it. */
 int fdas_destroy(fdas_plan p);
 

@@ -102,15 +102,11 @@ struct fdas_plan_s {
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
     int *d_status = nullptr;
     int64_t device_bytes = 0;
-    // batched form: work counter, graph [memset counter -> persistent kernel], host table
-    int *d_counter = nullptr;
+    // batched form: the resolved persistent kernel and the plan's own lane
     std::mutex batch_mu;
     fdas::BatchKernel bk;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    cudaGraphNode_t kernel_node = nullptr;
-    fdas::BatchTable *table = nullptr;      // host copy, 64-byte aligned
-    fdas::OlsArgs batch_args = {};
+    int bk_version = 0;                     // bumped whenever bk changes (graphs must be rebuilt)
+    fdas::Lane lane0;
     // autotuner results, ms per plane of the tuning array, [L index][G index]
     float tune_ms[3][3] = {};
     int tuned = 0;
@@ -134,10 +130,7 @@ void plan_free(fdas_plan p)
     cudaFree(p->d_status);
     cudaFree(p->d_in_stage);
     cudaFree(p->d_out_stage);
-    cudaFree(p->d_counter);
-    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-    if (p->graph) cudaGraphDestroy(p->graph);
-    if (p->table) ::operator delete(p->table, std::align_val_t(64));
+    fdas::lane_free(&p->lane0);
     for (auto &e : p->chunk_ev)
         if (e) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
@@ -200,44 +193,8 @@ int build_templates(fdas_plan p, const float2 *d_h32, int L)
     p->L = L;
     p->S = (L - p->K + 1) & ~3;
     p->bk = fdas::BatchKernel();
-    if (p->graph_exec) {
-        cudaGraphExecDestroy(p->graph_exec);
-        cudaGraphDestroy(p->graph);
-        p->graph_exec = nullptr;
-        p->graph = nullptr;
-    }
+    p->bk_version++;
     if ((e = fdas::batch_kernel(L, &p->bk)) != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
-    return FDAS_OK;
-}
-
-// Build the batch graph once: [memset work counter] -> [persistent kernel over all resident blocks].
-int ensure_graph(fdas_plan p)
-{
-    if (p->graph_exec) return FDAS_OK;
-    if (!p->table) {
-        p->table = static_cast<fdas::BatchTable *>(::operator new(sizeof(fdas::BatchTable), std::align_val_t(64)));
-        std::memset(p->table, 0, sizeof(fdas::BatchTable));
-    }
-    cudaError_t e;
-    if ((e = cudaGraphCreate(&p->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph create");
-    cudaMemsetParams mp = {};
-    mp.dst = p->d_counter;
-    mp.value = 0;
-    mp.elementSize = 4;
-    mp.width = 1;
-    mp.height = 1;
-    cudaGraphNode_t ms;
-    if ((e = cudaGraphAddMemsetNode(&ms, p->graph, nullptr, 0, &mp)) != cudaSuccess) return cuda_fail(e, "graph memset node");
-    void *args[3] = {p->table, &p->batch_args, &p->d_counter};
-    cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void *>(p->bk.fn);
-    kp.gridDim = dim3(p->bk.resident);
-    kp.blockDim = dim3(p->bk.block);
-    kp.sharedMemBytes = (unsigned)p->bk.smem;
-    kp.kernelParams = args;
-    if ((e = cudaGraphAddKernelNode(&p->kernel_node, p->graph, &ms, 1, &kp)) != cudaSuccess)
-        return cuda_fail(e, "graph kernel node");
-    if ((e = cudaGraphInstantiate(&p->graph_exec, p->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
     return FDAS_OK;
 }
 
@@ -252,60 +209,10 @@ int validate_batch(fdas_plan p, int count, const void *const *ins, const int64_t
     return FDAS_OK;
 }
 
-// Fill the table for arrays [first, first + cnt) and replay the graph on `stream`.
-int enqueue_batch_chunk(fdas_plan p, int first, int cnt, const void *const *ins, const int64_t *ns,
-                        float *const *outs, cudaStream_t stream)
-{
-    fdas::BatchTable &t = *p->table;
-    const int ngroups = (p->M + p->G - 1) / p->G;
-    int64_t items = 0;
-    for (int i = 0; i < cnt; ++i) {
-        fdas::BatchArray &a = t.arr[i];
-        int rc = encode_input_map(&a.map, ins[first + i], ns[first + i]);
-        if (rc) return rc;
-        a.out = outs[first + i];
-        a.n = ns[first + i];
-        a.nseg = (int)n_segments(p, a.n);
-        a.item_off = items;
-        items += (int64_t)a.nseg * ngroups;
-    }
-    t.count = cnt;
-    t.total_items = items;
-    fdas::OlsArgs &a = p->batch_args;
-    a.H = p->d_H;
-    a.tw = p->d_tw;
-    a.out = nullptr;
-    a.n = 0;
-    a.M = p->M;
-    a.G = p->G;
-    a.S = p->S;
-    a.K = p->K;
-    a.seg_begin = 0;
-    a.status = p->d_status;
-    void *args[3] = {p->table, &p->batch_args, &p->d_counter};
-    cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void *>(p->bk.fn);
-    kp.gridDim = dim3(p->bk.resident);
-    kp.blockDim = dim3(p->bk.block);
-    kp.sharedMemBytes = (unsigned)p->bk.smem;
-    kp.kernelParams = args;
-    cudaError_t e;
-    if ((e = cudaGraphExecKernelNodeSetParams(p->graph_exec, p->kernel_node, &kp)) != cudaSuccess)
-        return cuda_fail(e, "graph kernel params");
-    if ((e = cudaGraphLaunch(p->graph_exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
-    return FDAS_OK;
-}
-
 int enqueue_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs,
                   cudaStream_t stream)
 {
-    int rc = ensure_graph(p);
-    if (rc) return rc;
-    for (int first = 0; first < count; first += fdas::kBatchMax) {
-        const int cnt = std::min(fdas::kBatchMax, count - first);
-        if ((rc = enqueue_batch_chunk(p, first, cnt, ins, ns, outs, stream))) return rc;
-    }
-    return FDAS_OK;
+    return fdas::lane_launch(p, &p->lane0, count, ins, ns, outs, stream);
 }
 
 // Autotuner: time the persistent kernel for every (L, G) candidate on one array of
@@ -425,7 +332,7 @@ int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *
     cudaError_t e;
     if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * chunks, stream)) != cudaSuccess)
         return cuda_fail(e, "clear work counters");
-    alignas(64) BatchTable t;
+    BatchTable t;
     OlsArgs a = {};
     a.H = p->d_H;
     a.tw = p->d_tw;
@@ -457,6 +364,119 @@ int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *
     }
     return FDAS_OK;
 }
+
+void lane_free(Lane *l)
+{
+    if (l->exec) cudaGraphExecDestroy(l->exec);
+    if (l->graph) cudaGraphDestroy(l->graph);
+    cudaFree(l->d_counter);
+    if (l->table) ::operator delete(l->table, std::align_val_t(alignof(BatchTable)));
+    *l = Lane();
+}
+
+// Build (or rebuild after the plan's kernel changed) the lane's graph:
+// [memset work counter] -> [persistent kernel over all resident blocks].
+static int lane_ensure(fdas_plan p, Lane *l)
+{
+    cudaError_t e;
+    if (!l->d_counter) {
+        if ((e = cudaMalloc(&l->d_counter, 256)) != cudaSuccess) return cuda_fail(e, "cudaMalloc work counter");
+        if ((e = cudaMemset(l->d_counter, 0, 256)) != cudaSuccess) return cuda_fail(e, "memset work counter");
+    }
+    if (!l->table) {
+        l->table = static_cast<BatchTable *>(::operator new(sizeof(BatchTable), std::align_val_t(alignof(BatchTable)), std::nothrow));
+        if (!l->table) return fail(FDAS_ERR_OOM, "host batch table");
+        std::memset(l->table, 0, sizeof(BatchTable));
+    }
+    if (l->exec && l->version == p->bk_version) return FDAS_OK;
+    if (l->exec) cudaGraphExecDestroy(l->exec);
+    if (l->graph) cudaGraphDestroy(l->graph);
+    l->exec = nullptr;
+    l->graph = nullptr;
+    if ((e = cudaGraphCreate(&l->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph create");
+    cudaMemsetParams mp = {};
+    mp.dst = l->d_counter;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 1;
+    mp.height = 1;
+    cudaGraphNode_t ms;
+    if ((e = cudaGraphAddMemsetNode(&ms, l->graph, nullptr, 0, &mp)) != cudaSuccess) return cuda_fail(e, "graph memset node");
+    void *args[3] = {l->table, &l->args, &l->d_counter};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void *>(p->bk.fn);
+    kp.gridDim = dim3(p->bk.resident);
+    kp.blockDim = dim3(p->bk.block);
+    kp.sharedMemBytes = (unsigned)p->bk.smem;
+    kp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&l->kernel_node, l->graph, &ms, 1, &kp)) != cudaSuccess)
+        return cuda_fail(e, "graph kernel node");
+    if ((e = cudaGraphInstantiate(&l->exec, l->graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    l->version = p->bk_version;
+    return FDAS_OK;
+}
+
+// Fill the lane's table for arrays [first, first + cnt) and replay its graph on `stream`.
+static int lane_chunk(fdas_plan p, Lane *l, int first, int cnt, const void *const *ins, const int64_t *ns,
+                      float *const *outs, cudaStream_t stream)
+{
+    BatchTable &t = *l->table;
+    const int ngroups = (p->M + p->G - 1) / p->G;
+    int64_t items = 0;
+    for (int i = 0; i < cnt; ++i) {
+        BatchArray &a = t.arr[i];
+        int rc = encode_input_map(&a.map, ins[first + i], ns[first + i]);
+        if (rc) return rc;
+        a.out = outs[first + i];
+        a.n = ns[first + i];
+        a.nseg = (int)n_segments(p, a.n);
+        a.item_off = items;
+        items += (int64_t)a.nseg * ngroups;
+    }
+    t.count = cnt;
+    t.total_items = items;
+    OlsArgs &a = l->args;
+    a = OlsArgs();
+    a.H = p->d_H;
+    a.tw = p->d_tw;
+    a.M = p->M;
+    a.G = p->G;
+    a.S = p->S;
+    a.K = p->K;
+    a.status = p->d_status;
+    void *args[3] = {l->table, &l->args, &l->d_counter};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void *>(p->bk.fn);
+    kp.gridDim = dim3(p->bk.resident);
+    kp.blockDim = dim3(p->bk.block);
+    kp.sharedMemBytes = (unsigned)p->bk.smem;
+    kp.kernelParams = args;
+    cudaError_t e;
+    if ((e = cudaGraphExecKernelNodeSetParams(l->exec, l->kernel_node, &kp)) != cudaSuccess)
+        return cuda_fail(e, "graph kernel params");
+    if ((e = cudaGraphLaunch(l->exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    return FDAS_OK;
+}
+
+int lane_launch(fdas_plan p, Lane *l, int count, const void *const *ins, const int64_t *ns, float *const *outs,
+                cudaStream_t stream)
+{
+    int rc = lane_ensure(p, l);
+    if (rc) return rc;
+    for (int first = 0; first < count; first += kBatchMax) {
+        const int cnt = std::min(kBatchMax, count - first);
+        if ((rc = lane_chunk(p, l, first, cnt, ins, ns, outs, stream))) return rc;
+    }
+    return FDAS_OK;
+}
+
+int validate_array(fdas_plan p, const void *in, int64_t n, const float *out)
+{
+    return validate_convolve(p, in, n, out);
+}
+
+int plan_templates(fdas_plan p) { return p ? p->M : 0; }
+int64_t plan_n_max(fdas_plan p) { return p ? p->n_max : 0; }
 
 // Plan accessor and error reporting for code outside this file.
 int plan_device(fdas_plan p) { return p ? p->device : -1; }
@@ -521,9 +541,7 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     };
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc status"));
-    if ((e = cudaMalloc(&p->d_counter, 256)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc work counter"));
     if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup_fail(cuda_fail(e, "memset status"));
-    if ((e = cudaMemset(p->d_counter, 0, 256)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "memset counter"));
     float2 *d_h32 = nullptr;
     const size_t h_bytes = sizeof(float2) * (size_t)M * K;
     if ((e = cudaMalloc(&d_h32, h_bytes)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc template staging"));

@@ -54,7 +54,7 @@ struct OlsArgs {
 };
 
 // One array of a batch: its input tensor map (param space), output plane and work items.
-struct alignas(64) BatchArray {
+struct BatchArray {   // aligned as CUtensorMap
     CUtensorMap map;      // 1-D tiled map over the array's complex64 input
     float *out;           // [M][n]
     int64_t n;
@@ -63,12 +63,13 @@ struct alignas(64) BatchArray {
     int pad_;
 };
 constexpr int kBatchMax = 120;   // arrays per launch: the table is a kernel parameter (< 32 KB)
-struct alignas(64) BatchTable {
+struct BatchTable {
     int count;
     int pad_;
     int64_t total_items;
     BatchArray arr[kBatchMax];
 };
+static_assert(sizeof(BatchTable) + sizeof(OlsArgs) + sizeof(int *) <= 32764, "batch table must fit the kernel parameters");
 
 // Resolved persistent batch kernel for one segment length.
 struct BatchKernel {
@@ -78,6 +79,25 @@ struct BatchKernel {
     int resident = 0;     // blocks that fit on the device at once
 };
 cudaError_t batch_kernel(int L, BatchKernel *k);
+
+// A lane: one work counter, one host table and one graph [reset counter -> persistent
+// kernel]; batches on different lanes may run concurrently.
+struct Lane {
+    int *d_counter = nullptr;
+    BatchTable *table = nullptr;
+    OlsArgs args = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t kernel_node = nullptr;
+    int version = -1;
+};
+// Enqueue planes of `count` arrays (validated by the caller) on the lane, chunked by kBatchMax.
+int lane_launch(fdas_plan p, Lane *l, int count, const void *const *ins, const int64_t *ns, float *const *outs,
+                cudaStream_t stream);
+void lane_free(Lane *l);
+int validate_array(fdas_plan p, const void *in, int64_t n, const float *out);
+int plan_templates(fdas_plan p);
+int64_t plan_n_max(fdas_plan p);
 
 // Graph-free launches of the persistent batch kernel with caller-provided work counters
 // (one per table of kBatchMax arrays, at most max_chunks); clears them on the stream first.

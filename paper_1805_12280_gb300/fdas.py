@@ -46,6 +46,21 @@ class fdas_plan_desc(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9)]
 
 
+class fdas_server_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("lanes", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class fdas_server_report(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("peak_bytes_in_use", ctypes.c_int64), ("admission_waits", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("arrays_per_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 # Every exported symbol with (restype, argtypes).  The CPU tests check that the
 # library exports exactly what include/fdas.h declares.
 _P = ctypes.c_void_p
@@ -59,6 +74,13 @@ SIGNATURES = {
     "fdas_convolve_batch": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_convolve_batch_noalloc": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_plan_status": (_I, [_P, _P]),
+    "fdas_server_create": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(fdas_server_opts)]),
+    "fdas_server_submit": (_I, [_P, _P, _I64, ctypes.POINTER(_I64)]),
+    "fdas_server_wait": (_I, [_P, _I64, _I64, ctypes.POINTER(_P)]),
+    "fdas_server_release": (_I, [_P, _I64]),
+    "fdas_server_stats": (_I, [_P, ctypes.POINTER(fdas_server_report)]),
+    "fdas_server_reset_stats": (_I, [_P]),
+    "fdas_server_destroy": (_I, [_P]),
     "fdas_destroy": (_I, [_P]),
     "fdas_strerror": (ctypes.c_char_p, [_I]),
     "fdas_last_error": (ctypes.c_char_p, []),
@@ -146,6 +168,43 @@ def fdas_convolve_batch_noalloc(plan: int, in_ptrs, ns, out_ptrs, stream: int = 
 
 def fdas_plan_status(plan: int, stream: int = 0) -> None:
     _check(load().fdas_plan_status(_P(plan), _P(stream)), "fdas_plan_status")
+
+
+def fdas_server_create(plan: int, budget_bytes: int, lanes: int = 0, max_batch: int = 0) -> int:
+    h = _P()
+    opts = fdas_server_opts(int(budget_bytes), int(lanes), int(max_batch))
+    _check(load().fdas_server_create(ctypes.byref(h), _P(plan), ctypes.byref(opts)), "fdas_server_create")
+    return h.value
+
+
+def fdas_server_submit(server: int, in_ptr: int, n: int) -> int:
+    t = _I64()
+    _check(load().fdas_server_submit(_P(server), _P(in_ptr), int(n), ctypes.byref(t)), "fdas_server_submit")
+    return t.value
+
+
+def fdas_server_wait(server: int, ticket: int, timeout_ms: int = -1) -> int:
+    ptr = _P()
+    _check(load().fdas_server_wait(_P(server), int(ticket), int(timeout_ms), ctypes.byref(ptr)), "fdas_server_wait")
+    return ptr.value
+
+
+def fdas_server_release(server: int, ticket: int) -> None:
+    _check(load().fdas_server_release(_P(server), int(ticket)), "fdas_server_release")
+
+
+def fdas_server_stats(server: int) -> dict:
+    r = fdas_server_report()
+    _check(load().fdas_server_stats(_P(server), ctypes.byref(r)), "fdas_server_stats")
+    return r.as_dict()
+
+
+def fdas_server_reset_stats(server: int) -> None:
+    _check(load().fdas_server_reset_stats(_P(server)), "fdas_server_reset_stats")
+
+
+def fdas_server_destroy(server: int) -> None:
+    _check(load().fdas_server_destroy(_P(server)), "fdas_server_destroy")
 
 
 def fdas_destroy(plan: int) -> None:
@@ -238,3 +297,65 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching request loop over a Plan (the plan must outlive the server)."""
+
+    def __init__(self, plan: Plan, budget_bytes: int, lanes: int = 0, max_batch: int = 0):
+        self.plan = plan
+        self.handle = fdas_server_create(plan.handle, budget_bytes, lanes, max_batch)
+        self._keep = {}
+
+    def submit(self, x) -> int:
+        """Queue device array ``x`` (torch complex64); returns a ticket.  ``x`` is kept alive."""
+        t = fdas_server_submit(self.handle, x.data_ptr(), x.numel())
+        self._keep[t] = x
+        return t
+
+    def wait(self, ticket: int, timeout_ms: int = -1, n: int | None = None):
+        """Wait for the plane; returns its device address, or a torch view when ``n`` is given."""
+        ptr = fdas_server_wait(self.handle, ticket, timeout_ms)
+        if n is None:
+            return ptr
+        return _device_view(ptr, (self.plan.n_templates, n), self._keep[ticket].device)
+
+    def release(self, ticket: int) -> None:
+        fdas_server_release(self.handle, ticket)
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        return fdas_server_stats(self.handle)
+
+    def reset_stats(self) -> None:
+        fdas_server_reset_stats(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            fdas_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(ptr: int, shape, device):
+    """A torch float32 tensor viewing device memory owned by the library (no copy)."""
+    import torch
+
+    class _Array:
+        def __init__(self):
+            self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), False),
+                                             "version": 3, "strides": None}
+    with torch.cuda.device(device):
+        return torch.as_tensor(_Array(), device=device)
