@@ -146,10 +146,14 @@ def time_oracle_sample(x, h, seg_len, target_s):
     oracle.ols_power(x[:probe], h, L=seg_len)
     dt = time.perf_counter() - t0
     sample = int(min(n, max(probe, probe * target_s / max(dt, 1e-6))))
-    t0 = time.perf_counter()
-    oracle.ols_power(x[:sample], h, L=seg_len)
-    dt = time.perf_counter() - t0
-    return sample, dt, oracle.threads()
+    runs, t0 = 0, time.perf_counter()
+    while True:                       # repeat a whole-array sample until ~target_s of work
+        oracle.ols_power(x[:sample], h, L=seg_len)
+        runs += 1
+        if time.perf_counter() - t0 >= target_s or sample < n:
+            break
+    dt = (time.perf_counter() - t0) / runs
+    return sample, dt, oracle.threads(), runs
 
 
 def run_reference(args):
@@ -281,10 +285,16 @@ def run_fdas(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample, dt, cores = time_oracle_sample(x, h, args.seg_len, args.cpu_seconds)
+        sample, dt, cores, runs = time_oracle_sample(x, h, args.seg_len, args.cpu_seconds)
         cpu = {"value": (sample / n) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"FP64 overlap-save oracle (C, OpenMP) on the first {sample} of {n} bins of the same array, "
-                         f"85 templates, {dt:.1f} s, scaled to whole arrays"}
+                         f"85 templates, {runs} run(s) of {dt:.2f} s each, scaled to whole arrays"}
+
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        del out
+        torch.cuda.empty_cache()
+        forms = {"batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -294,12 +304,128 @@ def run_fdas(args):
                 "plane_gbs": 4.0 * m * n * world / (ms_per_step / 1e3) / 1e9,
                 "model_tflops": model_flops(n, m, args.seg_len, h.shape[1]) * world / (ms_per_step / 1e3) / 1e12,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
+                "forms": forms,
                 "gpu_launches": args.steps,
                 "vs_baseline_note": "paper: 3x Stratix V A7 FPGAs, 120 ms per 2^22 array, 84 filters (context)"}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _events_ms(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_batch(fd, h, dev, reps=10):
+    """Batched form: 64 dedispersion trials, N log-uniform in [2^18, 2^22], one persistent
+    launch per graph replay, (L, G) from the autotuner; beside it the same 64 arrays
+    through the per-array FP32 path (fdas_convolve, L = 2048, G = 85)."""
+    import torch
+    specs = synth.batch_trials()
+    xs = [torch.from_numpy(synth.make_input(s)).to(dev) for s in specs]
+    outs = [torch.empty((h.shape[0], x.numel()), dtype=torch.float32, device=dev) for x in xs]
+    total_n = sum(x.numel() for x in xs)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": "64 arrays, N log-uniform in [2^18, 2^22] (seeds 1000+i), 85 templates",
+           "arrays": len(xs), "total_points": total_n,
+           "plane_bytes": 4 * h.shape[0] * total_n}
+    with fd.Plan(h, n_max=1 << 22, autotune=1) as plan:
+        d = plan.desc
+        for _ in range(3):
+            plan.convolve_batch(xs, outs, stream)
+        ms = _events_ms(lambda: plan.convolve_batch(xs, outs, stream), reps, stream)
+        plan.status(stream)
+        res.update({"seg_len": d.seg_len, "tpl_per_cta": d.tpl_per_cta, "tune_ms": [round(v, 4) for v in d.tune_ms],
+                    "ms_per_batch": ms, "arrays_per_s": len(xs) / (ms / 1e3),
+                    "plane_gbs": res["plane_bytes"] / (ms / 1e3) / 1e9, "gpu_launches_per_batch": 1})
+    with fd.Plan(h, n_max=1 << 22) as plan:
+        def per_array():
+            for x, o in zip(xs, outs):
+                plan.convolve(x, o, stream)
+        per_array()
+        ms1 = _events_ms(per_array, max(2, reps // 2), stream)
+        res.update({"per_array_fp32_ms": ms1, "per_array_fp32_arrays_per_s": len(xs) / (ms1 / 1e3)})
+    del xs, outs
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=32, stress_budget=4e9,
+                stress_requests=300):
+    """Served form: Poisson arrivals at `rate`, N log-uniform in [2^16, 2^22], admission by
+    plane memory within `budget`; requests cycle over `pool_size` distinct arrays."""
+    import queue
+    import threading
+    import torch
+    count = int(rate * duration)
+    arrivals, specs = synth.poisson_requests(count, rate_hz=rate)
+    pool = [torch.from_numpy(synth.make_input(s)).to(dev) for s in specs[:pool_size]]
+    res = {"workload": f"Poisson {rate:g} arrays/s for {duration:g} s ({count} requests), N log-uniform in "
+                       f"[2^16, 2^22] (arrival seed 2000, {pool_size} distinct arrays 2001+i), budget "
+                       f"{budget / 1e9:g} GB", "requests": count}
+    with fd.Plan(h, n_max=1 << 22, tpl_per_cta=17) as plan:
+        stream = torch.cuda.current_stream(dev)
+        outs = [torch.empty((h.shape[0], x.numel()), dtype=torch.float32, device=dev) for x in pool]
+
+        def per_array():
+            for x, o in zip(pool, outs):
+                plan.convolve(x, o, stream)
+        per_array()
+        ms1 = _events_ms(per_array, 3, stream)
+        mean_n = np.mean([x.numel() for x in pool])
+        res["per_array_fp32_ms_mean"] = ms1 / len(pool)
+        res["per_array_fp32_capacity_arrays_per_s"] = len(pool) / (ms1 / 1e3)
+        del outs
+
+        def run(srv, times):
+            q = queue.Queue()
+
+            def consumer():
+                while True:
+                    t = q.get()
+                    if t is None:
+                        return
+                    srv.wait(t)
+                    srv.release(t)
+            th = threading.Thread(target=consumer)
+            th.start()
+            t0 = time.perf_counter()
+            for i, ta in enumerate(times):
+                delay = t0 + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                q.put(srv.submit(pool[i % len(pool)]))
+            q.put(None)
+            th.join()
+            return srv.stats()
+
+        with fd.Server(plan, budget_bytes=int(budget), lanes=2, max_batch=32) as srv:
+            run(srv, np.zeros(len(pool)))                     # warm-up
+            srv.reset_stats()
+            st = run(srv, arrivals)
+        res.update({"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                    "max_ms": st["max_ms"], "sustained_arrays_per_s": st["arrays_per_s"],
+                    "completed": st["completed"], "launches": st["launches"],
+                    "admission_waits": st["admission_waits"], "peak_plane_gb": st["peak_bytes_in_use"] / 1e9})
+        with fd.Server(plan, budget_bytes=int(stress_budget), lanes=2, max_batch=32) as srv:
+            run(srv, np.zeros(len(pool)))
+            srv.reset_stats()
+            st = run(srv, np.zeros(stress_requests))           # all at once: saturation
+        res["stress"] = {"budget_gb": stress_budget / 1e9, "requests": stress_requests,
+                         "arrays_per_s": st["arrays_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                         "admission_waits": st["admission_waits"], "peak_plane_gb": st["peak_bytes_in_use"] / 1e9}
+        res["mean_n"] = float(mean_n)
+    del pool
+    torch.cuda.empty_cache()
+    return res
 
 
 def profile_traffic():
@@ -332,6 +458,7 @@ def main():
     ap.add_argument("--tpl-per-cta", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)
     args = ap.parse_args()
