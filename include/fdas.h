@@ -40,7 +40,9 @@ extern "C" {
 
 /* Arithmetic forms of the segment FFTs. */
 #define FDAS_PREC_FP32          0     /* FP32 CUDA-core FFTs (default) */
-#define FDAS_PREC_TC_BF16X3     1     /* tensor-core DFT-GEMM stages, bf16 hi/lo split, FP32 accumulate */
+#define FDAS_PREC_TC_FP16       1     /* tensor-core DFT-GEMM stages for the inverse FFT's radix-16
+                                         passes: fp16 data, fp16 hi/lo-split DFT matrices, FP32
+                                         accumulation; needs seg_len 2048 */
 
 typedef struct fdas_plan_s *fdas_plan;
 

@@ -100,6 +100,7 @@ struct fdas_plan_s {
     float2 *d_tw = nullptr;     // [L] FP32 twiddles
     double2 *d_tw64 = nullptr;  // [L] FP64 twiddles
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
+    unsigned char *d_wtc = nullptr;   // tensor-core form: real 32x32 DFT matrices (hi/lo fp16)
     int *d_status = nullptr;
     int64_t device_bytes = 0;
     // batched form: the resolved persistent kernel and the plan's own lane
@@ -127,6 +128,7 @@ void plan_free(fdas_plan p)
     cudaFree(p->d_tw);
     cudaFree(p->d_tw64);
     cudaFree(p->d_H);
+    cudaFree(p->d_wtc);
     cudaFree(p->d_status);
     cudaFree(p->d_in_stage);
     cudaFree(p->d_out_stage);
@@ -166,7 +168,8 @@ int enqueue_segments(fdas_plan p, const CUtensorMap *map, int64_t n, float *out,
     a.K = p->K;
     a.seg_begin = (int)s0;
     a.status = p->d_status;
-    cudaError_t e = fdas::launch_ols_fp32(p->L, map, a, (int)(s1 - s0), stream);
+    cudaError_t e = p->precision == FDAS_PREC_TC_FP16 ? fdas::launch_ols_tc(map, a, p->d_wtc, (int)(s1 - s0), stream)
+                                                       : fdas::launch_ols_fp32(p->L, map, a, (int)(s1 - s0), stream);
     if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch");
     return FDAS_OK;
 }
@@ -513,7 +516,10 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     if (opts) o = *opts;
     const int L = o.seg_len ? o.seg_len : 2048;
     if (L != 1024 && L != 2048 && L != 4096) return fail(FDAS_ERR_INVALID_ARG, "seg_len %d not in {1024, 2048, 4096}", L);
-    if (o.precision != FDAS_PREC_FP32) return fail(FDAS_ERR_UNSUPPORTED, "precision %d not built", o.precision);
+    if (o.precision != FDAS_PREC_FP32 && o.precision != FDAS_PREC_TC_FP16)
+        return fail(FDAS_ERR_UNSUPPORTED, "precision %d not built", o.precision);
+    if (o.precision == FDAS_PREC_TC_FP16 && (L != 2048 || o.autotune))
+        return fail(FDAS_ERR_UNSUPPORTED, "the tensor-core form is built for seg_len 2048 without autotuning");
     if (!templates) return fail(FDAS_ERR_INVALID_ARG, "null templates");
     if (M < 1) return fail(FDAS_ERR_INVALID_ARG, "n_templates=%d < 1", M);
     if (K < 1 || K > L - 4) return fail(FDAS_ERR_INVALID_ARG, "tpl_len=%d outside [1, %d]", K, L - 4);
@@ -550,12 +556,17 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
         return cleanup_fail(cuda_fail(e, "copy templates"));
     }
     int rc = FDAS_OK;
-    if (o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
+    if (p->precision == FDAS_PREC_TC_FP16) {
+        if ((e = cudaMalloc(&p->d_wtc, fdas::tc_matrix_bytes())) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc DFT matrices");
+        else if ((e = fdas::launch_tc_matrices(p->d_wtc, nullptr)) != cudaSuccess) rc = cuda_fail(e, "DFT matrix kernel");
+    }
+    if (rc == FDAS_OK && o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
     if (rc == FDAS_OK) rc = build_templates(p, d_h32, p->L);
     cudaFree(d_h32);
     if (rc != FDAS_OK) return cleanup_fail(rc);
     p->device_bytes = (int64_t)(sizeof(float2) * p->L + sizeof(double2) * p->L +
-                                sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) + 256);
+                                sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) +
+                                (p->d_wtc ? fdas::tc_matrix_bytes() : 0));
     *out = p;
     return FDAS_OK;
 }

@@ -111,6 +111,12 @@ cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, in
                             cudaStream_t s);
 size_t ols_fp32_smem_bytes(int L);
 
+// Tensor-core form (L = 2048): the real DFT matrices (plan time) and the segment kernel.
+cudaError_t launch_tc_matrices(unsigned char *wmat, cudaStream_t s);
+size_t tc_matrix_bytes();
+cudaError_t launch_ols_tc(const CUtensorMap *tmap, const OlsArgs &a, const unsigned char *wmat, int nseg,
+                          cudaStream_t s);
+
 // Plan-time kernels (FP64).
 cudaError_t launch_twiddles(int L, double2 *w64, float2 *w32, cudaStream_t s);
 cudaError_t launch_pretransform(int L, const float2 *h32, int M, int K, const double2 *w64,

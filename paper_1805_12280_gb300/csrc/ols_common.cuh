@@ -1,0 +1,59 @@
+// Forward segment FFT shared by the FP32 and tensor-core segment kernels.
+#pragma once
+#include "fdas_internal.cuh"
+#include "fft_regs.cuh"
+
+namespace fdas {
+
+// Forward L-point FFT of the segment in e1 (natural order) by the NT = L/16 threads of a
+// block: passes A and B exchange through e2 and e1, pass C leaves the spectrum in X
+// ("C distribution": slot g*R + k3 of thread t holds X[k1 + 16 k2 + 16 Q k3] with
+// k1 = t % 16, k2 = t / 16 + (NT/16) g).  Ends before the barrier that must follow it.
+template <int L>
+__device__ __forceinline__ void forward_fft(float2 *e1, float2 *e2, const float2 *__restrict__ tw, float2 (&v)[16],
+                                            float2 (&X)[16])
+{
+    using Gm = Geo<L>;
+    constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
+    constexpr int MASK = L - 1;
+    const int tid = threadIdx.x, k1 = tid & 15, hi = tid >> 4;
+    // ---- forward pass A: 16-point DFT over the top digit, twiddle W_L^{t k1}
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = e1[j * NT + tid];
+    dft<16, -1>(v);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(&tw[(tid * k) & MASK]));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) e2[tid + LD2 * k] = v[k];
+    __syncthreads();
+    // ---- forward pass B: Q-point DFT over b, twiddle W_{QR}^{c k2}
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) v[g * Q + b] = e2[(b * R + cg) + LD2 * k1];
+    }
+    dft<Q, -1, 1, 0>(v);
+    if constexpr (GB == 2) dft<Q, -1, 1, Q>(v);
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+            const float2 w = (k2 == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[(16 * cg * k2) & MASK]);
+            e1[k1 + 16 * k2 + 16 * Q * cg] = cmul(v[g * Q + k2], w);
+        }
+    }
+    __syncthreads();
+    // ---- forward pass C: R-point DFT over c; spectrum stays in registers
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        const int k2 = hi + (NT / 16) * g;
+#pragma unroll
+        for (int c = 0; c < R; ++c) X[g * R + c] = e1[k1 + 16 * k2 + 16 * Q * c];
+    }
+    dft<R, -1, 1, 0>(X);
+    if constexpr (GC == 2) dft<R, -1, 1, R>(X);
+}
+
+}  // namespace fdas

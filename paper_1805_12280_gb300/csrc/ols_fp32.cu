@@ -19,6 +19,7 @@
 
 #include "fdas_internal.cuh"
 #include "fft_regs.cuh"
+#include "ols_common.cuh"
 #include "ptx.cuh"
 
 // Minimum resident blocks per SM requested from the compiler (caps registers per thread).
@@ -145,43 +146,7 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     }
 
     float2 v[16], X[16];
-    // ---- forward pass A: 16-point DFT over the top digit, twiddle W_L^{t k1}
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = e1[j * NT + tid];
-    dft<16, -1>(v);
-#pragma unroll
-    for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(&a.tw[(tid * k) & MASK]));
-#pragma unroll
-    for (int k = 0; k < 16; ++k) e2[tid + LD2 * k] = v[k];
-    __syncthreads();
-    // ---- forward pass B: Q-point DFT over b, twiddle W_{QR}^{c k2}
-#pragma unroll
-    for (int g = 0; g < GB; ++g) {
-        const int cg = hi + (NT / 16) * g;
-#pragma unroll
-        for (int b = 0; b < Q; ++b) v[g * Q + b] = e2[(b * R + cg) + LD2 * k1];
-    }
-    dft<Q, -1, 1, 0>(v);
-    if constexpr (GB == 2) dft<Q, -1, 1, Q>(v);
-#pragma unroll
-    for (int g = 0; g < GB; ++g) {
-        const int cg = hi + (NT / 16) * g;
-#pragma unroll
-        for (int k2 = 0; k2 < Q; ++k2) {
-            const float2 w = (k2 == 0) ? make_float2(1.f, 0.f) : __ldg(&a.tw[(16 * cg * k2) & MASK]);
-            e1[k1 + 16 * k2 + 16 * Q * cg] = cmul(v[g * Q + k2], w);
-        }
-    }
-    __syncthreads();
-    // ---- forward pass C: R-point DFT over c; spectrum stays in registers
-#pragma unroll
-    for (int g = 0; g < GC; ++g) {
-        const int k2 = hi + (NT / 16) * g;
-#pragma unroll
-        for (int c = 0; c < R; ++c) X[g * R + c] = e1[k1 + 16 * k2 + 16 * Q * c];
-    }
-    dft<R, -1, 1, 0>(X);
-    if constexpr (GC == 2) dft<R, -1, 1, R>(X);
+    forward_fft<L>(e1, e2, a.tw, v, X);
     __syncthreads();   // every thread has read e1 before the template loop rewrites it
 
     const int64_t seg_out = (int64_t)seg * a.S;                 // first output index of this segment

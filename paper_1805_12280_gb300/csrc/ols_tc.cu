@@ -1,0 +1,329 @@
+// Tensor-core form of the overlap-save segment kernel (L = 2048).
+//
+// Same work item and forward FFT as the FP32 kernel.  Per template, the inverse FFT's two
+// radix-16 passes (B' over k2, A' over k1) are dense DFT-matrix GEMMs on the 5th-generation
+// tensor cores: each pass is D[128 x 32] = A[128 x 32] . W[32 x 32] with the complex
+// 16-point inverse DFT written as a real 32 x 32 matrix, A = the 128 sub-transform rows of
+// one template's data in fp16 (staged in shared memory), W split into fp16 hi + lo parts
+// (two MMAs per K-step recover the DFT matrix to ~2^-22), FP32 accumulation in tensor
+// memory.  The product with H_z, the radix-8 pass C', the inter-pass twiddles, the discard
+// and |y|^2 stay on the CUDA cores in FP32.  B' uses W/16 and A' uses 16 W (exact power-of-2
+// scalings) so that the fp16 operand of A' stays far from the fp16 range limit.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "fdas_internal.cuh"
+#include "fft_regs.cuh"
+#include "ols_common.cuh"
+#include "ptx.cuh"
+
+namespace fdas {
+
+namespace tc {
+
+constexpr int L = 2048, NT = 128, Q = 16, R = 8, LD2 = NT + 1;
+// A operand [128 rows x 32 fp16], K-major, no swizzle: core matrices of 8 rows x 16 bytes;
+// LBO = stride between core matrices along K, SBO = stride between 8-row groups.
+constexpr uint32_t A_LBO = 160, A_SBO = 640;            // padded: conflict-free A' writes
+constexpr uint32_t A_BYTES = 16 * A_SBO;                // 10240
+// B operand (the DFT matrix) [32 rows (n) x 32 fp16 (k)], K-major, no swizzle.
+constexpr uint32_t B_LBO = 128, B_SBO = 512, B_BYTES = 4 * B_SBO;   // 2048 per matrix
+constexpr uint32_t W_BYTES = 4 * B_BYTES;               // B' hi, B' lo, A' hi, A' lo
+constexpr uint32_t H_BYTES = sizeof(float2) * L;
+constexpr uint32_t TMEM_COLS = 64;                      // D of B' (32) and of A' (32)
+// kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
+constexpr uint32_t IDESC = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct Smem {
+    static constexpr size_t e1 = 0;                                  // segment / B' A-operand
+    static constexpr size_t e2 = e1 + sizeof(float2) * L;            // exchange / A' A-operand
+    static constexpr size_t hb = e2 + sizeof(float2) * 16 * LD2;     // template double buffer
+    static constexpr size_t wm = (hb + 2 * H_BYTES + 127) & ~size_t(127);
+    static constexpr size_t bar = wm + W_BYTES;                      // 4 mbarriers
+    static constexpr size_t slot = bar + 4 * 8;                      // TMEM address
+    static constexpr size_t total = 128 + slot + 16;
+    static_assert(sizeof(float2) * L >= A_BYTES && sizeof(float2) * 16 * LD2 >= A_BYTES, "operand aliasing");
+};
+
+__host__ __device__ inline uint32_t a_off(int r, int k)
+{
+    return (uint32_t)((r >> 3) * A_SBO + (k >> 3) * A_LBO + (r & 7) * 16 + (k & 7) * 2);
+}
+__host__ __device__ inline uint32_t b_off(int n, int k)
+{
+    return (uint32_t)((n >> 3) * B_SBO + (k >> 3) * B_LBO + (n & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive fp32 columns of this thread's TMEM lane (warp w reads lanes 32w..32w+31).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&f)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void st_h2(unsigned char *base, uint32_t off, float re, float im)
+{
+    const __half2 h = __floats2half2_rn(re, im);
+    *reinterpret_cast<__half2 *>(base + off) = h;
+}
+
+// The four real 32 x 32 DFT matrices, written once per plan in the B-operand layout.
+__global__ void tc_matrix_kernel(unsigned char *out)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (matrix-pair p, n, k)
+    if (idx >= 2 * 32 * 32) return;
+    const int p = idx / 1024, n = (idx / 32) % 32, k = idx % 32;
+    const int b = n >> 1, ro = n & 1, kk = k >> 1, ri = k & 1;
+    double s, c;
+    sincospi(2.0 * (double)((kk * b) & 15) / 16.0, &s, &c);   // inverse 16-point DFT, exp(+2 pi i kk b / 16)
+    const double scale = p == 0 ? 1.0 / 16.0 : 16.0;         // B' pass, A' pass
+    // real form of (re_in + i im_in) * (c + i s): out_re = re c - im s, out_im = re s + im c
+    double w;
+    if (ro == 0) w = ri == 0 ? c : -s;
+    else w = ri == 0 ? s : c;
+    w *= scale;
+    const __half hi = __double2half(w);
+    const __half lo = __double2half(w - (double)__half2float(hi));
+    __half *base = reinterpret_cast<__half *>(out + (size_t)p * 2 * B_BYTES);
+    base[b_off(n, k) / 2] = hi;
+    base[(B_BYTES + b_off(n, k)) / 2] = lo;
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(128, 1)
+    ols_tc_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a, const unsigned char *__restrict__ wmat)
+{
+    using namespace tc;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2 *e1 = reinterpret_cast<float2 *>(sm + Smem::e1);
+    float2 *e2 = reinterpret_cast<float2 *>(sm + Smem::e2);
+    float4 *hb = reinterpret_cast<float4 *>(sm + Smem::hb);
+    unsigned char *wm = sm + Smem::wm;
+    unsigned char *aB = sm + Smem::e1;   // A operand of B' (aliases the segment buffer)
+    unsigned char *aA = sm + Smem::e2;   // A operand of A' (aliases exchange buffer 2)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Smem::bar);   // [0] segment+W, [1],[2] templates, [3] MMA
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Smem::slot);
+
+    const int tid = threadIdx.x, warp = tid >> 5, k1 = tid & 15, hi = tid >> 4;
+    const int seg = a.seg_begin + blockIdx.x;
+    const int z0 = blockIdx.y * a.G, z1 = min(z0 + a.G, a.M);
+
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)) + W_BYTES);
+        const int c0 = seg * a.S - (a.K - 1);
+#pragma unroll
+        for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, &bar[0]);
+        bulk_load(wm, wmat, W_BYTES, &bar[0]);
+        for (int i = 0; i < 2 && z0 + i < z1; ++i) {
+            mbar_arrive_expect_tx(&bar[1 + i], H_BYTES);
+            bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, H_BYTES, &bar[1 + i]);
+        }
+    }
+    // Inverse twiddles: C' output (W_{QR}^{-c k2}) and B' output (W_L^{-(bR + c) k1}).
+    float2 tw1[16], tw2[16];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const int k2 = hi + 8 * g;
+#pragma unroll
+        for (int c = 0; c < R; ++c) tw1[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & (L - 1)]));
+    }
+#pragma unroll
+    for (int b = 0; b < Q; ++b) tw2[b] = cconj(__ldg(&a.tw[((b * R + hi) * k1) & (L - 1)]));
+
+    const bool seg_ok = __syncthreads_and(mbar_wait_bounded(&bar[0], 0, kWaitLimitNs));
+    bool ok = seg_ok;
+    uint32_t h_uses[2] = {0, 0}, h_issued[2] = {z0 < z1, z0 + 1 < z1}, mma_uses = 0, mma_done = 0;
+    float2 v[16], X[16];
+    if (ok) {
+        forward_fft<L>(e1, e2, a.tw, v, X);
+        __syncthreads();   // e1/e2 are free: they become the A operands
+    }
+    const int64_t seg_out = (int64_t)seg * a.S;
+    const int64_t nvalid64 = a.n - seg_out;
+    const unsigned nvalid = (unsigned)(nvalid64 < a.S ? nvalid64 : a.S);
+    const int obase = tid - (a.K - 1);
+    const uint32_t aB_addr = smem_u32(aB), aA_addr = smem_u32(aA), w_addr = smem_u32(wm);
+
+    for (int z = z0; ok && z < z1; ++z) {
+        const int buf = (z - z0) & 1;
+        const float4 *hz = hb + buf * 8 * NT;
+        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], h_uses[buf] & 1, kWaitLimitNs);
+        h_uses[buf]++;
+        // ---- product with H_z, pass C' (radix 8, CUDA cores), twiddle, fp16 rows of B'
+#pragma unroll
+        for (int jp = 0; jp < 8; ++jp) {
+            const float4 h = hz[jp * NT + tid];
+            v[2 * jp] = cmul(X[2 * jp], make_float2(h.x, h.y));
+            v[2 * jp + 1] = cmul(X[2 * jp + 1], make_float2(h.z, h.w));
+        }
+        dft<R, 1, 1, 0>(v);
+        dft<R, 1, 1, R>(v);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int k2 = hi + 8 * g;
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+                const float2 y = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
+                st_h2(aB, a_off(k1 + 16 * c, 2 * k2), y.x, y.y);   // row (k1, c), K pair k2
+            }
+        }
+        fence_proxy_async_smem();
+        fence_before_sync();
+        if (!__syncthreads_and(h_ok)) {
+            ok = false;
+            break;
+        }
+        // every thread has read hb[buf]: refill it with the template two ahead
+        if (tid == 0) {
+            fence_after_sync();
+            if (z + 2 < z1) {
+                h_issued[buf]++;
+                mbar_arrive_expect_tx(&bar[1 + buf], H_BYTES);
+                bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + 2) * 8 * NT, H_BYTES, &bar[1 + buf]);
+            }
+            // ---- pass B': D_B = A_B . (W_hi + W_lo) / 16 over K = 32 (two K-steps)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ad = smem_desc(aB_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
+                mma_f16(tmem, ad, smem_desc(w_addr + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
+                mma_f16(tmem, ad, smem_desc(w_addr + B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
+            }
+            mma_commit(&bar[3]);
+        }
+        const bool mb_ok = mbar_wait_bounded(&bar[3], mma_uses & 1, kWaitLimitNs);
+        mma_uses++;
+        mma_done += mb_ok;
+        fence_after_sync();
+        // ---- B' output: row tid = (k1, c = tid / 16), columns (re, im) of b = 0..15
+        float f[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), f);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const float2 y = cmul(make_float2(f[2 * b], f[2 * b + 1]), tw2[b]);
+            st_h2(aA, a_off(b * R + hi, 2 * k1), y.x, y.y);       // row t = bR + c, K pair k1
+        }
+        fence_proxy_async_smem();
+        fence_before_sync();
+        if (!__syncthreads_and(mb_ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            fence_after_sync();
+            // ---- pass A': D_A = A_A . 16 (W_hi + W_lo)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ad = smem_desc(aA_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
+                mma_f16(tmem + 32, ad, smem_desc(w_addr + 2 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
+                mma_f16(tmem + 32, ad, smem_desc(w_addr + 3 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
+            }
+            mma_commit(&bar[3]);
+        }
+        const bool ma_one = mbar_wait_bounded(&bar[3], mma_uses & 1, kWaitLimitNs);
+        mma_uses++;
+        mma_done += ma_one;
+        const bool ma_ok = __syncthreads_and(ma_one);
+        fence_after_sync();
+        if (!ma_ok) {
+            ok = false;
+            break;
+        }
+        // ---- A' output: row t = tid holds y[a*NT + t], a = 0..15; discard, power, store
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32, f);
+        float *orow = a.out + (size_t)z * (size_t)a.n + seg_out;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int o = j * NT + obase;
+            if ((unsigned)o < nvalid) orow[o] = fmaf(f[2 * j], f[2 * j], f[2 * j + 1] * f[2 * j + 1]);
+        }
+        fence_before_sync();   // TMEM reads are ordered before the next template's MMAs
+    }
+    if (!ok && tid == 0) {   // give outstanding copies and MMAs a bounded time to land
+        atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+        if (!seg_ok) mbar_wait_bounded(&bar[0], 0, kWaitLimitNs);
+        for (int b = 0; b < 2; ++b)
+            if (h_issued[b] > h_uses[b]) mbar_wait_bounded(&bar[1 + b], h_uses[b] & 1, kWaitLimitNs);
+        if (mma_done < mma_uses) mbar_wait_bounded(&bar[3], (mma_uses - 1) & 1, kWaitLimitNs);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+cudaError_t launch_tc_matrices(unsigned char *wmat, cudaStream_t s)
+{
+    tc::tc_matrix_kernel<<<(2 * 32 * 32 + 255) / 256, 256, 0, s>>>(wmat);
+    return cudaGetLastError();
+}
+
+size_t tc_matrix_bytes() { return tc::W_BYTES; }
+
+cudaError_t launch_ols_tc(const CUtensorMap *tmap, const OlsArgs &a, const unsigned char *wmat, int nseg,
+                          cudaStream_t s)
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+        e = cudaFuncSetAttribute(ols_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::Smem::total);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    dim3 grid(nseg, (a.M + a.G - 1) / a.G);
+    ols_tc_kernel<<<grid, 128, tc::Smem::total, s>>>(*tmap, a, wmat);
+    return cudaGetLastError();
+}
+
+}  // namespace fdas

@@ -25,7 +25,7 @@ FDAS_ERR_REJECTED = -6
 FDAS_ERR_UNSUPPORTED = -7
 
 FDAS_PREC_FP32 = 0
-FDAS_PREC_TC_BF16X3 = 1
+FDAS_PREC_TC_FP16 = 1
 
 
 class FdasError(RuntimeError):
