@@ -194,9 +194,9 @@ def run_reference(args):
 
 def workload_config(args, n, tpl_len):
     return {"workload": f"single SKA-sized array: N=2^{int(np.log2(n))} complex64, 85 templates (<= {tpl_len} taps), "
-                        f"L={args.seg_len} overlap-save, fp32 power plane",
+                        f"L={args.seg_len} overlap-save, {args.precision} segment FFTs, fp32 power plane",
             "n": n, "templates": 85, "tpl_len": tpl_len, "seg_len": args.seg_len,
-            "tpl_per_cta": args.tpl_per_cta or 85, "precision": "fp32",
+            "tpl_per_cta": args.tpl_per_cta or 85, "precision": args.precision,
             "l2": "no flush: each step writes the 1.43 GB plane (> 129 MB L2), evicting the 33.5 MB input"}
 
 
@@ -214,7 +214,8 @@ def run_fdas(args):
     x = synth.make_input(spec)
     h, _ = synth.template_bank()
     n, m = x.size, h.shape[0]
-    plan = fd.Plan(h, n_max=n, seg_len=args.seg_len, tpl_per_cta=args.tpl_per_cta)
+    prec = fd.FDAS_PREC_TC_FP16 if args.precision == "tc" else fd.FDAS_PREC_FP32
+    plan = fd.Plan(h, n_max=n, seg_len=args.seg_len, tpl_per_cta=args.tpl_per_cta, precision=prec)
     stream = torch.cuda.current_stream(dev)
     xd = torch.from_numpy(x).to(dev)
     out = torch.empty((m, n), dtype=torch.float32, device=dev)
@@ -280,7 +281,8 @@ def run_fdas(args):
     achieved = alg / (kern_ms / 1e3) / 1e9
     traffic = profile_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "ols_fp32_kernel<2048>",
+                "traffic": traffic if args.precision == "fp32" else None, "peak_kind": peak_kind,
+                "kernel": "ols_fp32_kernel<2048>" if args.precision == "fp32" else "ols_tc_kernel",
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kern_ms}
 
     cpu = None
@@ -294,7 +296,8 @@ def run_fdas(args):
     if rank == 0 and world == 1 and not args.no_forms:
         del out
         torch.cuda.empty_cache()
-        forms = {"batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
+        forms = {"tensor_core": bench_tc(fd, h, dev, xd), "batched": bench_batch(fd, h, dev),
+                 "served": bench_serve(fd, h, dev)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -322,6 +325,29 @@ def _events_ms(fn, reps, stream):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def bench_tc(fd, h, dev, xd, reps=50):
+    """Tensor-core form on the same array: radix-16 inverse passes as fp16 DFT-GEMMs
+    (hi/lo DFT matrices, FP32 accumulation); beside it the FP32 kernel, same (L, G)."""
+    import torch
+    n, m = xd.numel(), h.shape[0]
+    out = torch.empty((m, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": "N=2^22, 85 templates, L=2048, G=85 (same array as the headline)"}
+    for name, prec in (("tc_fp16", fd.FDAS_PREC_TC_FP16), ("fp32", fd.FDAS_PREC_FP32)):
+        with fd.Plan(h, n_max=n, precision=prec) as plan:
+            for _ in range(3):
+                plan.convolve(xd, out, stream)
+            ms = _events_ms(lambda: plan.convolve(xd, out, stream), reps, stream)
+            plan.status(stream)
+        res[name] = {"ms_per_array": ms, "arrays_per_s": 1e3 / ms,
+                     "hbm_frac": algorithmic_bytes(n, m) / (ms / 1e3) / 1e9 / measured_peaks()[0]}
+    res["accuracy"] = ("tests/test_gpu_tc.py: max |P - P_ref| / max P_ref < 1e-3 against the FP64 oracle "
+                       "(tolerance 2e-3), strong-candidate sets identical")
+    del out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_batch(fd, h, dev, reps=10):
@@ -456,6 +482,8 @@ def main():
     ap.add_argument("--seg-len", type=int, default=2048)
     ap.add_argument("--log2n", type=int, default=22, help="array length 2^log2n (22 = the SKA-sized workload)")
     ap.add_argument("--tpl-per-cta", type=int, default=0)
+    ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
+                    help="segment-kernel arithmetic of the timed steps (tc: tensor-core DFT-GEMM passes)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")

@@ -56,7 +56,8 @@ struct Block {
     float2 *e2;      // exchange buffer 2 [16][NT + 1]
     float4 *hb;      // template double buffer [2][8][NT]
     uint64_t *bar;   // [0] segment, [1], [2] template buffers
-    uint32_t seg_uses = 0, h_uses[2] = {0, 0};   // completed phases per barrier
+    uint32_t seg_uses = 0, h_uses0 = 0, h_uses1 = 0;   // completed phases per barrier (scalars:
+                                                       // a runtime-indexed array would spill to local memory)
 
     __device__ explicit Block(unsigned char *raw)
     {
@@ -139,7 +140,7 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
         if (tid == 0) {
             atomicOr(a.status, STATUS_WAIT_TIMEOUT);
             const unsigned pending = 1u | 2u | (z0 + 1 < z1 ? 4u : 0u);
-            const unsigned parity = ((B.seg_uses - 1) & 1u) | ((B.h_uses[0] & 1u) << 1) | ((B.h_uses[1] & 1u) << 2);
+            const unsigned parity = ((B.seg_uses - 1) & 1u) | ((B.h_uses0 & 1u) << 1) | ((B.h_uses1 & 1u) << 2);
             drain(bar, pending, parity);
         }
         return false;
@@ -157,8 +158,9 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     for (int z = z0; z < z1; ++z) {
         const int buf = (z - z0) & 1;
         const float4 *hz = hb + buf * 8 * NT;
-        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], B.h_uses[buf] & 1, kWaitLimitNs);
-        B.h_uses[buf]++;
+        const uint32_t hu = buf ? B.h_uses1 : B.h_uses0;
+        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], hu & 1, kWaitLimitNs);
+        if (buf) B.h_uses1++; else B.h_uses0++;
         // ---- element-wise product with H_z (1/L folded in)
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
@@ -181,7 +183,8 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
                 atomicOr(a.status, STATUS_WAIT_TIMEOUT);
                 const int other = 1 - buf;
                 const unsigned pending = (2u << buf) | (z + 1 < z1 ? (2u << other) : 0u);
-                const unsigned parity = (((B.h_uses[buf] - 1) & 1u) << (1 + buf)) | ((B.h_uses[other] & 1u) << (1 + other));
+                const uint32_t hb_ = buf ? B.h_uses1 : B.h_uses0, ho_ = buf ? B.h_uses0 : B.h_uses1;
+                const unsigned parity = (((hb_ - 1) & 1u) << (1 + buf)) | ((ho_ & 1u) << (1 + other));
                 drain(bar, pending, parity);
             }
             return false;

@@ -40,8 +40,8 @@ struct Smem {
     static constexpr size_t e2 = e1 + sizeof(float2) * L;            // exchange / A' A-operand
     static constexpr size_t hb = e2 + sizeof(float2) * 16 * LD2;     // template double buffer
     static constexpr size_t wm = (hb + 2 * H_BYTES + 127) & ~size_t(127);
-    static constexpr size_t bar = wm + W_BYTES;                      // 4 mbarriers
-    static constexpr size_t slot = bar + 4 * 8;                      // TMEM address
+    static constexpr size_t bar = wm + W_BYTES;                      // 5 mbarriers
+    static constexpr size_t slot = bar + 5 * 8;                      // TMEM address
     static constexpr size_t total = 128 + slot + 16;
     static_assert(sizeof(float2) * L >= A_BYTES && sizeof(float2) * 16 * LD2 >= A_BYTES, "operand aliasing");
 };
@@ -125,7 +125,10 @@ __global__ void tc_matrix_kernel(unsigned char *out)
 
 }  // namespace tc
 
-__global__ void __launch_bounds__(128, 1)
+#ifndef FDAS_TC_MINB
+#define FDAS_TC_MINB 1
+#endif
+__global__ void __launch_bounds__(128, FDAS_TC_MINB)
     ols_tc_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a, const unsigned char *__restrict__ wmat)
 {
     using namespace tc;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(128, 1)
     unsigned char *wm = sm + Smem::wm;
     unsigned char *aB = sm + Smem::e1;   // A operand of B' (aliases the segment buffer)
     unsigned char *aA = sm + Smem::e2;   // A operand of A' (aliases exchange buffer 2)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Smem::bar);   // [0] segment+W, [1],[2] templates, [3] MMA
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Smem::bar);   // [0] segment+W, [1],[2] templates, [3] B' MMA, [4] A' MMA
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Smem::slot);
 
     const int tid = threadIdx.x, warp = tid >> 5, k1 = tid & 15, hi = tid >> 4;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(128, 1)
     const int z0 = blockIdx.y * a.G, z1 = min(z0 + a.G, a.M);
 
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < 5; ++i) mbar_init(&bar[i], 1);
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -182,7 +185,9 @@ __global__ void __launch_bounds__(128, 1)
 
     const bool seg_ok = __syncthreads_and(mbar_wait_bounded(&bar[0], 0, kWaitLimitNs));
     bool ok = seg_ok;
-    uint32_t h_uses[2] = {0, 0}, h_issued[2] = {z0 < z1, z0 + 1 < z1}, mma_uses = 0, mma_done = 0;
+    // per-buffer counters as scalars (a runtime-indexed array would live in local memory)
+    uint32_t h_uses0 = 0, h_uses1 = 0, h_iss0 = z0 < z1, h_iss1 = z0 + 1 < z1;
+    uint32_t b_uses = 0, b_done = 0, a_uses = 0, a_done = 0;   // MMA completions awaited / seen
     float2 v[16], X[16];
     if (ok) {
         forward_fft<L>(e1, e2, a.tw, v, X);
@@ -194,12 +199,17 @@ __global__ void __launch_bounds__(128, 1)
     const int obase = tid - (a.K - 1);
     const uint32_t aB_addr = smem_u32(aB), aA_addr = smem_u32(aA), w_addr = smem_u32(wm);
 
+    // Software pipeline over templates: the B' MMA of template z runs while the threads
+    // finish template z-1 (A' output, power, stores); the A' MMA of template z runs while
+    // they prepare template z+1 (product, C', B' operand).
+    float f[32];
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     for (int z = z0; ok && z < z1; ++z) {
         const int buf = (z - z0) & 1;
         const float4 *hz = hb + buf * 8 * NT;
-        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], h_uses[buf] & 1, kWaitLimitNs);
-        h_uses[buf]++;
-        // ---- product with H_z, pass C' (radix 8, CUDA cores), twiddle, fp16 rows of B'
+        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], (buf ? h_uses1 : h_uses0) & 1, kWaitLimitNs);
+        if (buf) h_uses1++; else h_uses0++;
+        // ---- S1(z): product with H_z, pass C' (radix 8, CUDA cores), twiddle, fp16 rows of B'
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
             const float4 h = hz[jp * NT + tid];
@@ -223,15 +233,15 @@ __global__ void __launch_bounds__(128, 1)
             ok = false;
             break;
         }
-        // every thread has read hb[buf]: refill it with the template two ahead
         if (tid == 0) {
             fence_after_sync();
+            // every thread has read hb[buf]: refill it with the template two ahead
             if (z + 2 < z1) {
-                h_issued[buf]++;
+                if (buf) h_iss1++; else h_iss0++;
                 mbar_arrive_expect_tx(&bar[1 + buf], H_BYTES);
                 bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + 2) * 8 * NT, H_BYTES, &bar[1 + buf]);
             }
-            // ---- pass B': D_B = A_B . (W_hi + W_lo) / 16 over K = 32 (two K-steps)
+            // ---- pass B'(z): D_B = A_B . (W_hi + W_lo) / 16 over K = 32 (two K-steps)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 const uint64_t ad = smem_desc(aB_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
@@ -240,13 +250,27 @@ __global__ void __launch_bounds__(128, 1)
             }
             mma_commit(&bar[3]);
         }
-        const bool mb_ok = mbar_wait_bounded(&bar[3], mma_uses & 1, kWaitLimitNs);
-        mma_uses++;
-        mma_done += mb_ok;
+        // ---- S3(z-1): A' output of the previous template -> discard, power, store
+        bool ma_ok = true;
+        if (z > z0) {
+            ma_ok = mbar_wait_bounded(&bar[4], a_uses & 1, kWaitLimitNs);
+            a_uses++;
+            a_done += ma_ok;
+            fence_after_sync();
+            tmem_ld32(tmem + lane_base + 32, f);
+            float *orow = a.out + (size_t)(z - 1) * (size_t)a.n + seg_out;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int o = j * NT + obase;
+                if ((unsigned)o < nvalid) orow[o] = fmaf(f[2 * j], f[2 * j], f[2 * j + 1] * f[2 * j + 1]);
+            }
+        }
+        // ---- S2(z): B' output row tid = (k1, c = tid / 16), columns (re, im) of b = 0..15
+        const bool mb_ok = mbar_wait_bounded(&bar[3], b_uses & 1, kWaitLimitNs);
+        b_uses++;
+        b_done += mb_ok;
         fence_after_sync();
-        // ---- B' output: row tid = (k1, c = tid / 16), columns (re, im) of b = 0..15
-        float f[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), f);
+        tmem_ld32(tmem + lane_base, f);
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             const float2 y = cmul(make_float2(f[2 * b], f[2 * b + 1]), tw2[b]);
@@ -254,46 +278,44 @@ __global__ void __launch_bounds__(128, 1)
         }
         fence_proxy_async_smem();
         fence_before_sync();
-        if (!__syncthreads_and(mb_ok)) {
+        if (!__syncthreads_and(mb_ok && ma_ok)) {
             ok = false;
             break;
         }
         if (tid == 0) {
             fence_after_sync();
-            // ---- pass A': D_A = A_A . 16 (W_hi + W_lo)
+            // ---- pass A'(z): D_A = A_A . 16 (W_hi + W_lo)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 const uint64_t ad = smem_desc(aA_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
                 mma_f16(tmem + 32, ad, smem_desc(w_addr + 2 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
                 mma_f16(tmem + 32, ad, smem_desc(w_addr + 3 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
             }
-            mma_commit(&bar[3]);
+            mma_commit(&bar[4]);
         }
-        const bool ma_one = mbar_wait_bounded(&bar[3], mma_uses & 1, kWaitLimitNs);
-        mma_uses++;
-        mma_done += ma_one;
-        const bool ma_ok = __syncthreads_and(ma_one);
+    }
+    // ---- drain: A' output of the last template
+    if (ok && z1 > z0) {
+        const bool ma_ok = mbar_wait_bounded(&bar[4], a_uses & 1, kWaitLimitNs);
+        a_uses++;
+        a_done += ma_ok;
         fence_after_sync();
-        if (!ma_ok) {
-            ok = false;
-            break;
-        }
-        // ---- A' output: row t = tid holds y[a*NT + t], a = 0..15; discard, power, store
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32, f);
-        float *orow = a.out + (size_t)z * (size_t)a.n + seg_out;
+        tmem_ld32(tmem + lane_base + 32, f);
+        float *orow = a.out + (size_t)(z1 - 1) * (size_t)a.n + seg_out;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int o = j * NT + obase;
             if ((unsigned)o < nvalid) orow[o] = fmaf(f[2 * j], f[2 * j], f[2 * j + 1] * f[2 * j + 1]);
         }
-        fence_before_sync();   // TMEM reads are ordered before the next template's MMAs
+        ok = __syncthreads_and(ma_ok);
     }
     if (!ok && tid == 0) {   // give outstanding copies and MMAs a bounded time to land
         atomicOr(a.status, STATUS_WAIT_TIMEOUT);
         if (!seg_ok) mbar_wait_bounded(&bar[0], 0, kWaitLimitNs);
-        for (int b = 0; b < 2; ++b)
-            if (h_issued[b] > h_uses[b]) mbar_wait_bounded(&bar[1 + b], h_uses[b] & 1, kWaitLimitNs);
-        if (mma_done < mma_uses) mbar_wait_bounded(&bar[3], (mma_uses - 1) & 1, kWaitLimitNs);
+        if (h_iss0 > h_uses0) mbar_wait_bounded(&bar[1], h_uses0 & 1, kWaitLimitNs);
+        if (h_iss1 > h_uses1) mbar_wait_bounded(&bar[2], h_uses1 & 1, kWaitLimitNs);
+        if (b_done < b_uses) mbar_wait_bounded(&bar[3], (b_uses - 1) & 1, kWaitLimitNs);
+        if (a_done < a_uses) mbar_wait_bounded(&bar[4], (a_uses - 1) & 1, kWaitLimitNs);
     }
     fence_before_sync();
     __syncthreads();
