@@ -279,9 +279,9 @@ def run_fdas(args):
     peak, peak_kind = measured_peaks()
     alg = algorithmic_bytes(n, m)
     achieved = alg / (kern_ms / 1e3) / 1e9
-    traffic = profile_traffic()
+    traffic = profile_traffic(args.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic if args.precision == "fp32" else None, "peak_kind": peak_kind,
+                "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "ols_fp32_kernel<2048>" if args.precision == "fp32" else "ols_tc_kernel",
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kern_ms}
 
@@ -454,19 +454,27 @@ def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=3
     return res
 
 
-def profile_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel build."""
-    path = os.path.join(ROOT, "profiles", "ols_fp32_L2048_n2p22_traffic.json")
+KERNEL_SOURCES = {"fp32": ("ols_fp32.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "fdas_internal.cuh"),
+                  "tc": ("ols_tc.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "fdas_internal.cuh")}
+
+
+def kernel_sources_sha256(precision: str) -> str:
+    import hashlib
+    src = os.path.join(ROOT, "paper_1805_12280_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in KERNEL_SOURCES[precision]:
+        with open(os.path.join(src, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(precision: str = "fp32"):
+    """DRAM bytes per launch from the committed ncu record, if it matches this kernel's sources."""
+    path = os.path.join(ROOT, "profiles", f"ols_{precision}_L2048_n2p22_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        import hashlib
-        src = os.path.join(ROOT, "paper_1805_12280_gb300", "csrc")
-        hsh = hashlib.sha256()
-        for fn in sorted(os.listdir(src)):
-            if fn.startswith(("ols_fp32", "fft_regs", "ptx")):
-                hsh.update(open(os.path.join(src, fn), "rb").read())
-        if d.get("kernel_sources_sha256") != hsh.hexdigest():
+        if d.get("kernel_sources_sha256") != kernel_sources_sha256(precision):
             return None
         return d.get("dram_bytes_per_launch")
     except Exception:
