@@ -62,7 +62,8 @@ typedef struct {
     int64_t n_max;        /* largest array length accepted */
     int     n_templates;  /* M */
     int     tpl_len;      /* K as given */
-    int     frame_len;    /* K used internally (K, or K+1 with a trailing zero tap when K is even) */
+    int     frame_len;    /* K used internally: K padded with up to 3 trailing zero taps so that
+                             frame_len - 1 is a multiple of 4 (the convolution is unchanged) */
     int     seg_len;      /* L */
     int     seg_step;     /* S: valid outputs per segment, a multiple of 4, <= L - frame_len + 1 */
     int     tpl_per_cta;  /* G */

@@ -535,7 +535,8 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     p->n_max = n_max;
     p->M = M;
     p->K_user = K;
-    p->K = (K % 2 == 0) ? K + 1 : K;           // odd frame: segment starts stay 16-byte aligned
+    p->K = 4 * ((K - 1 + 3) / 4) + 1;           // frame with K-1 a multiple of 4 (trailing zero taps):
+                                                // segment starts and row segments stay 16-byte aligned
     p->L = L;
     p->S = (L - p->K + 1) & ~3;                 // multiple of 4, <= L - K + 1
     p->G = o.tpl_per_cta ? o.tpl_per_cta : M;

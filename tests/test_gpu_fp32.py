@@ -164,3 +164,19 @@ def test_ska_array_full_plane_vs_ols_oracle(fd, oracle_mod, bank):
         m = 42 + int(c.z)
         i = int(round(c.r + c.z / 2)) + 210
         assert p[m, i - 3:i + 4].max() > 20 * np.median(p[m])
+
+
+def test_plane_pointer_alignment_paths(fd, bank):
+    # a 16-byte-aligned plane with n % 4 == 0 leaves through bulk copies from shared memory;
+    # a plane that is only 4-byte aligned takes the per-thread store path: same bits
+    rng = np.random.default_rng(13)
+    n = 8000
+    x = torch.from_numpy((rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)).cuda()
+    with fd.Plan(bank[::9], n_max=n) as plan:
+        m = plan.n_templates
+        ref = plan.convolve(x)
+        buf = torch.full((m * n + 4,), -1.0, dtype=torch.float32, device="cuda")
+        for shift in (1, 2, 3):
+            fd.fdas_convolve(plan.handle, x.data_ptr(), n, buf.data_ptr() + 4 * shift)
+            plan.status()
+            assert torch.equal(buf[shift:shift + m * n].view(m, n), ref)
