@@ -49,6 +49,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_array_spec(rank: int, log2n: int = 22):
+    """Each rank processes its own dedispersion trial (replicas: no data exchange)."""
+    return synth.single_ska(n=1 << log2n, seed=1 + rank)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """MAX of a per-rank float over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, units_per_rank: int, max_elapsed_s: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / max_elapsed_s
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -210,7 +232,7 @@ def run_fdas(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = synth.single_ska(n=1 << args.log2n, seed=1 + rank)   # each rank its own dedispersion trial
+    spec = rank_array_spec(rank, args.log2n)
     x = synth.make_input(spec)
     h, _ = synth.template_bank()
     n, m = x.size, h.shape[0]
@@ -244,14 +266,10 @@ def run_fdas(args):
     if world > 1:
         torch.distributed.barrier()
     plan.status(stream)
-    elapsed_ms = t_start.elapsed_time(t_end)
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     ms_per_step = elapsed_ms / args.steps
-    value = world * args.steps / (elapsed_ms / 1e3)
+    value = aggregate_rate(world, args.steps, elapsed_ms / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -267,12 +285,8 @@ def run_fdas(args):
         t0 = time.perf_counter()
         for _ in range(ks):
             plan.convolve_host(xh_np, oh_np)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * ks / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * m * n,
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": aggregate_rate(world, ks, dt), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * m * n,
                "steps": ks, "api": "fdas_convolve_host (pinned host buffers)"}
         del xh, oh
 
@@ -284,6 +298,13 @@ def run_fdas(args):
                 "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "ols_fp32_kernel<2048>" if args.precision == "fp32" else "ols_tc_kernel",
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kern_ms}
+
+    # Second roofline: the paper's operation count (Table 1, C = 5) against the FP32 CUDA-core
+    # peak of this GPU (152 SMs x 128 FP32 lanes x 2 flop per FMA x the sampled SM clock).
+    flops = model_flops(n, m, args.seg_len, h.shape[1])
+    roofline_alu = {"bound": "alu", "achieved": flops / (kern_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                    "flops_per_launch": flops, "note": "paper operation count (Table 1, C=5); the kernel is "
+                    "bound by FP32 instruction issue (see profiles/)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -299,6 +320,10 @@ def run_fdas(args):
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "batched": bench_batch(fd, h, dev),
                  "served": bench_serve(fd, h, dev)}
 
+    clock_summary = clocks.summary()
+    sm_mhz = clock_summary.get("sm_mhz") or clock_summary.get("sm_max_mhz") or 2070.0
+    roofline_alu["peak"] = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    roofline_alu["frac"] = roofline_alu["achieved"] / roofline_alu["peak"]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -306,7 +331,8 @@ def run_fdas(args):
                 "config": workload_config(args, n, h.shape[1]),
                 "plane_gbs": 4.0 * m * n * world / (ms_per_step / 1e3) / 1e9,
                 "model_tflops": model_flops(n, m, args.seg_len, h.shape[1]) * world / (ms_per_step / 1e3) / 1e12,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
+                "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clock_summary,
                 "forms": forms,
                 "gpu_launches": args.steps,
                 "vs_baseline_note": "paper: 3x Stratix V A7 FPGAs, 120 ms per 2^22 array, 84 filters (context)"}
