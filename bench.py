@@ -317,8 +317,9 @@ def run_fdas(args):
     if rank == 0 and world == 1 and not args.no_forms:
         del out
         torch.cuda.empty_cache()
-        forms = {"tensor_core": bench_tc(fd, h, dev, xd), "batched": bench_batch(fd, h, dev),
-                 "served": bench_serve(fd, h, dev)}
+        forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
+                 "library_unfused_ols": bench_library_ols(h, dev, xd),
+                 "batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
 
     clock_summary = clocks.summary()
     sm_mhz = clock_summary.get("sm_mhz") or clock_summary.get("sm_max_mhz") or 2070.0
@@ -374,6 +375,76 @@ def bench_tc(fd, h, dev, xd, reps=50):
     del out
     torch.cuda.empty_cache()
     return res
+
+
+def bench_candidates(fd, h, dev, xd, x_host, reps=50, threshold=7.0):
+    """Fused threshold epilogue (fdas_convolve_candidates): same array, the plane is never
+    written; end to end: pinned input -> device -> candidates -> host list."""
+    import torch
+    n = xd.numel()
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": f"N=2^22, 85 templates, L=2048, G=85, threshold {threshold:g} (6 sigma)"}
+    with fd.Plan(h, n_max=n) as plan:
+        buf = torch.empty((1 << 22, 2), dtype=torch.int64, device=dev)
+        cnt = torch.empty(1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            plan.candidates(xd, threshold, buf.shape[0], stream, buf, cnt)
+        ms = _events_ms(lambda: plan.candidates(xd, threshold, buf.shape[0], stream, buf, cnt), reps, stream)
+        ncand = int(cnt.item())
+        res.update({"ms_per_array": ms, "arrays_per_s": 1e3 / ms, "candidates_per_array": ncand,
+                    "candidate_bytes": 16 * ncand})
+        xh = torch.from_numpy(x_host).pin_memory()
+        hbuf = torch.empty((buf.shape[0], 2), dtype=torch.int64).pin_memory()
+        hcnt = torch.empty(1, dtype=torch.int64).pin_memory()
+        xin = torch.empty_like(xd)
+
+        def e2e_step():
+            xin.copy_(xh, non_blocking=True)
+            plan.candidates(xin, threshold, buf.shape[0], stream, buf, cnt)
+            hcnt.copy_(cnt, non_blocking=False)
+            k = min(int(hcnt.item()), buf.shape[0])
+            hbuf[:k].copy_(buf[:k], non_blocking=False)
+        for _ in range(2):
+            e2e_step()
+        steps = 20
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / steps
+        plan.status(stream)
+        res["e2e"] = {"arrays_per_s": 1.0 / dt, "h2d_bytes": 8 * n, "d2h_bytes": 8 + 16 * ncand,
+                      "api": "fdas_convolve_candidates with pinned host input and candidate list"}
+    return res
+
+
+def bench_library_ols(h, dev, xd, reps=5, seg_len=2048):
+    """Same-GPU library comparison (not the product path): unfused overlap-save with
+    torch.fft (cuFFT) -- segment gather, batched FFT, product with all templates, batched
+    inverse FFT, discard, |y|^2 -- timed with CUDA events on the same array."""
+    import torch
+    n, (m, k) = xd.numel(), h.shape
+    S = seg_len - k + 1
+    nseg = (n + S - 1) // S
+    H = torch.fft.fft(torch.from_numpy(h).to(dev), n=seg_len)             # [M, L]
+    pad = torch.zeros(k - 1 + nseg * S + seg_len, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((m, nseg * S), dtype=torch.float32, device=dev)
+    chunk = 128                                                          # segments per step (memory)
+
+    def run():
+        pad[k - 1:k - 1 + n].copy_(xd)
+        seg = pad.unfold(0, seg_len, S)[:nseg]                           # [nseg, L] views
+        for c0 in range(0, nseg, chunk):
+            X = torch.fft.fft(seg[c0:c0 + chunk])                        # [c, L]
+            y = torch.fft.ifft(X[:, None, :] * H[None, :, :])            # [c, M, L]
+            p = y[..., k - 1:].abs().square()                            # [c, M, S]
+            out[:, c0 * S:(c0 + p.shape[0]) * S] = p.permute(1, 0, 2).reshape(m, -1)
+    run()
+    ms = _events_ms(run, reps, stream)
+    del out, pad, H
+    torch.cuda.empty_cache()
+    return {"what": "torch.fft (cuFFT) unfused overlap-save, 128 segments per step, same array and templates",
+            "ms_per_array": ms, "arrays_per_s": 1e3 / ms}
 
 
 def bench_batch(fd, h, dev, reps=10):

@@ -113,6 +113,33 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *desc);
 int fdas_convolve(fdas_plan p, const void *in_c64_dev, int64_t n, float *out_power_dev,
                   void *stream);
 
+/* One threshold crossing of the power plane. */
+typedef struct {
+    int32_t tpl;     /* template (row) index */
+    float   power;   /* P[tpl][bin], bit-identical to the plane fdas_convolve writes */
+    int64_t bin;     /* output index i, 0 <= i < n */
+} fdas_candidate;
+
+/*
+ * fdas_convolve_candidates -- the candidates of one array instead of its plane.
+ *
+ * The FT-convolution module sends the power plane on to candidate detection (Sec. 3);
+ * this entry point fuses the first step of that, the threshold, into the store epilogue
+ * of the segment kernel: every (tpl, bin) with P[tpl][bin] > threshold is appended to
+ * cand_dev, and the plane itself is never written to memory.
+ *
+ *   in_c64_dev : device complex64 [n], 16-byte aligned;  1 <= n <= n_max.
+ *   cand_dev   : device array of max_cand fdas_candidate (max_cand >= 0).
+ *   count_dev  : device pointer to one unsigned 64-bit counter; the library clears it on
+ *                `stream` before the launch; afterwards it holds the number of crossings
+ *                found, which may exceed max_cand (then only max_cand were stored).
+ * The order of the stored candidates is unspecified.  Asynchronous.  FP32 form only.
+ * Errors: INVALID_ARG, UNSUPPORTED (tensor-core plan), CUDA.
+ */
+int fdas_convolve_candidates(fdas_plan p, const void *in_c64_dev, int64_t n, float threshold,
+                             fdas_candidate *cand_dev, int64_t max_cand,
+                             unsigned long long *count_dev, void *stream);
+
 /*
  * fdas_convolve_host -- the same computation from and to host memory.
  *

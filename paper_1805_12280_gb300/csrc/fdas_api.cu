@@ -613,6 +613,44 @@ int fdas_convolve(fdas_plan p, const void *in, int64_t n, float *out, void *stre
     return enqueue_segments(p, &map, n, out, 0, n_segments(p, n), (cudaStream_t)stream);
 }
 
+int fdas_convolve_candidates(fdas_plan p, const void *in, int64_t n, float threshold, fdas_candidate *cand,
+                             int64_t max_cand, unsigned long long *count, void *stream)
+{
+    if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");
+    if (!in || !count || (max_cand > 0 && !cand)) return fail(FDAS_ERR_INVALID_ARG, "null pointer");
+    if (max_cand < 0) return fail(FDAS_ERR_INVALID_ARG, "max_cand < 0");
+    if (n < 1 || n > p->n_max) return fail(FDAS_ERR_INVALID_ARG, "n=%lld outside [1, n_max=%lld]", (long long)n, (long long)p->n_max);
+    if (reinterpret_cast<uintptr_t>(in) % 16) return fail(FDAS_ERR_INVALID_ARG, "input pointer must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(count) % 8 || reinterpret_cast<uintptr_t>(cand) % 8)
+        return fail(FDAS_ERR_INVALID_ARG, "counter and candidate array must be 8-byte aligned");
+    if (p->precision != FDAS_PREC_FP32) return fail(FDAS_ERR_UNSUPPORTED, "candidates are built for the FP32 form");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(FDAS_ERR_CUDA, "cannot select plan device %d", p->device);
+    CUtensorMap map;
+    int rc = encode_input_map(&map, in, n);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    FDAS_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s), "clear candidate counter");
+    fdas::OlsArgs a;
+    a.H = p->d_H;
+    a.tw = p->d_tw;
+    a.out = nullptr;
+    a.n = n;
+    a.M = p->M;
+    a.G = p->G;
+    a.S = p->S;
+    a.K = p->K;
+    a.seg_begin = 0;
+    a.status = p->d_status;
+    a.cand = cand ? cand : reinterpret_cast<fdas_candidate *>(count);   // non-null selects the epilogue
+    a.cand_count = count;
+    a.cand_max = max_cand;
+    a.threshold = threshold;
+    cudaError_t e = fdas::launch_ols_fp32(p->L, &map, a, (int)n_segments(p, n), s);
+    if (e != cudaSuccess) return cuda_fail(e, "candidate kernel launch");
+    return FDAS_OK;
+}
+
 int fdas_convolve_host(fdas_plan p, const void *in_host, int64_t n, float *out_host, void *stream)
 {
     if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");

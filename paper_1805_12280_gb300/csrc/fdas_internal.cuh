@@ -51,6 +51,11 @@ struct OlsArgs {
     int M, G, S, K;       // templates, templates per CTA, segment step, frame length
     int seg_begin;        // first segment of this launch
     int *status;          // device status word (bit 0: a bounded wait ran out)
+    // candidate epilogue (fdas_convolve_candidates): crossings of `threshold`
+    fdas_candidate *cand = nullptr;
+    unsigned long long *cand_count = nullptr;
+    long long cand_max = 0;
+    float threshold = 0.f;
 };
 
 // One array of a batch: its input tensor map (param space), output plane and work items.
@@ -106,7 +111,8 @@ int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *
 int plan_device(fdas_plan p);
 int set_error(int code, const char *msg);   // records the thread-local message, returns code
 
-// Launch the FP32 segment kernel over segments [seg_begin, seg_begin + nseg).
+// Launch the FP32 segment kernel over segments [seg_begin, seg_begin + nseg); with a.cand
+// set, the candidate epilogue replaces the plane stores.
 cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, int nseg,
                             cudaStream_t s);
 size_t ols_fp32_smem_bytes(int L);

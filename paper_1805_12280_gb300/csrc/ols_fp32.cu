@@ -108,7 +108,7 @@ __device__ __noinline__ void drain(uint64_t *bar, unsigned pending, unsigned par
 // One work item.  Every thread of the block calls it with the same arguments after a
 // block-wide barrier that follows the previous item.  Returns false (block-uniformly)
 // if a bounded wait ran out; the status bit is then set.
-template <int L>
+template <int L, bool CAND = false>
 __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CUtensorMap *map, int seg, int z0,
                                          int z1, int64_t n, float *out, const float2 (&tw1)[16],
                                          const float2 (&tw2)[16])
@@ -215,18 +215,47 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
         for (int k = 0; k < 16; ++k) v[k] = e2[tid + LD2 * k];
         dft<16, 1>(v);
         // ---- discard the first K-1 points, power, store the valid ones
-        float *orow = out + (size_t)z * (size_t)n + seg_out;
+        if constexpr (CAND) {
+            // threshold crossings instead of the plane: one atomic per warp and slot
+            const int lane = tid & 31;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int o = j * NT + obase;
-            if ((unsigned)o < nvalid) orow[o] = cabs2(v[j]);
+            for (int j = 0; j < 16; ++j) {
+                const int o = j * NT + obase;
+                const float pw = cabs2(v[j]);
+                const bool hit = (unsigned)o < nvalid && pw > a.threshold;
+                const unsigned mask = __ballot_sync(0xffffffffu, hit);
+                if (mask) {
+                    const int leader = __ffs(mask) - 1;
+                    unsigned long long base = 0;
+                    if (lane == leader) base = atomicAdd(a.cand_count, (unsigned long long)__popc(mask));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (hit) {
+                        const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+                        if (idx < (unsigned long long)a.cand_max) {
+                            fdas_candidate c;
+                            c.tpl = z;
+                            c.power = pw;
+                            c.bin = seg_out + o;
+                            a.cand[idx] = c;
+                        }
+                    }
+                }
+            }
+        } else {
+            float *orow = out + (size_t)z * (size_t)n + seg_out;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int o = j * NT + obase;
+                if ((unsigned)o < nvalid) orow[o] = cabs2(v[j]);
+            }
         }
     }
     return true;
 }
 
 // One item per block: blockIdx.x = segment (from a.seg_begin), blockIdx.y = template group.
-template <int L, int MINB>
+// CAND: candidate epilogue instead of the plane stores.
+template <int L, int MINB, bool CAND>
 __global__ void __launch_bounds__(L / 16, MINB)
     ols_fp32_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a)
 {
@@ -235,7 +264,7 @@ __global__ void __launch_bounds__(L / 16, MINB)
     float2 tw1[16], tw2[16];
     init_block<L>(B, a, tw1, tw2);
     const int z0 = blockIdx.y * a.G;
-    run_item<L>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out, tw1, tw2);
+    run_item<L, CAND>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out, tw1, tw2);
 }
 
 // Persistent: resident blocks take items (array, group, segment) from *counter until the
@@ -281,16 +310,22 @@ static cudaError_t set_smem_attr(const void *fn, bool *done)
     return e;
 }
 
-template <int L>
-static cudaError_t launch_l(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
+template <int L, bool CAND>
+static cudaError_t launch_lc(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
 {
-    auto kern = ols_fp32_kernel<L, minb<L>()>;
+    auto kern = ols_fp32_kernel<L, minb<L>(), CAND>;
     static bool done[64] = {};
     cudaError_t e = set_smem_attr<L>((const void *)kern, done);
     if (e != cudaSuccess) return e;
     dim3 grid(nseg, (a.M + a.G - 1) / a.G);
     kern<<<grid, L / 16, Smem<L>::total, s>>>(*tmap, a);
     return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_l(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
+{
+    return a.cand ? launch_lc<L, true>(tmap, a, nseg, s) : launch_lc<L, false>(tmap, a, nseg, s);
 }
 
 cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)

@@ -46,6 +46,13 @@ class fdas_plan_desc(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9)]
 
 
+class fdas_candidate(ctypes.Structure):
+    _fields_ = [("tpl", ctypes.c_int32), ("power", ctypes.c_float), ("bin", ctypes.c_int64)]
+
+
+CANDIDATE_DTYPE = np.dtype([("tpl", "<i4"), ("power", "<f4"), ("bin", "<i8")])
+
+
 class fdas_server_opts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("lanes", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
@@ -72,6 +79,7 @@ SIGNATURES = {
     "fdas_convolve": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_host": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_batch": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
+    "fdas_convolve_candidates": (_I, [_P, _P, _I64, ctypes.c_float, _P, _I64, _P, _P]),
     "fdas_convolve_batch_noalloc": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_plan_status": (_I, [_P, _P]),
     "fdas_server_create": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(fdas_server_opts)]),
@@ -142,6 +150,12 @@ def fdas_convolve(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0)
 
 def fdas_convolve_host(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
     _check(load().fdas_convolve_host(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_convolve_host")
+
+
+def fdas_convolve_candidates(plan: int, in_ptr: int, n: int, threshold: float, cand_ptr: int, max_cand: int,
+                             count_ptr: int, stream: int = 0) -> None:
+    _check(load().fdas_convolve_candidates(_P(plan), _P(in_ptr), int(n), float(threshold), _P(cand_ptr),
+                                           int(max_cand), _P(count_ptr), _P(stream)), "fdas_convolve_candidates")
 
 
 def fdas_convolve_batch(plan: int, in_ptrs, ns, out_ptrs, stream: int = 0) -> None:
@@ -251,6 +265,24 @@ class Plan:
         fdas_convolve(self.handle, x.data_ptr(), n, out.data_ptr(), _stream_handle(stream))
         return out
 
+    def candidates(self, x, threshold: float = 7.0, max_cand: int = 1 << 20, stream=None, buf=None, count=None):
+        """Threshold crossings of the plane of device array ``x`` (the plane is not written).
+
+        Returns (buf, count): ``buf`` a device int64 tensor [max_cand, 2] holding fdas_candidate
+        records, ``count`` a device int64 tensor [1] with the number of crossings found.
+        ``candidates_to_numpy`` decodes them on the host.
+        """
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        if buf is None:
+            buf = torch.empty((max(max_cand, 1), 2), dtype=torch.int64, device=x.device)
+        if count is None:
+            count = torch.empty(1, dtype=torch.int64, device=x.device)
+        fdas_convolve_candidates(self.handle, x.data_ptr(), x.numel(), threshold, buf.data_ptr(),
+                                 min(max_cand, buf.shape[0]), count.data_ptr(), _stream_handle(stream))
+        return buf, count
+
     def convolve_batch(self, xs, outs=None, stream=None):
         """Power planes of a list of device arrays in one persistent launch."""
         import torch
@@ -359,3 +391,10 @@ def _device_view(ptr: int, shape, device):
                                              "version": 3, "strides": None}
     with torch.cuda.device(device):
         return torch.as_tensor(_Array(), device=device)
+
+
+def candidates_to_numpy(buf, count) -> np.ndarray:
+    """Host copy of the stored candidates as a structured array (tpl, power, bin)."""
+    n = int(count.item()) if hasattr(count, "item") else int(count)
+    n = min(n, buf.shape[0])
+    return buf[:n].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1)

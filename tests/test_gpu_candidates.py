@@ -1,0 +1,90 @@
+"""GPU tests of the fused threshold epilogue (fdas_convolve_candidates)."""
+import numpy as np
+import pytest
+
+import synth
+from parity import THRESHOLD, TOL_FP32
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_12280_gb300 as fd
+    fd.load()
+    return fd
+
+
+@pytest.fixture(scope="module")
+def bank():
+    return synth.template_bank()[0]
+
+
+def _keys(c):
+    order = np.lexsort((c["bin"], c["tpl"]))
+    return c[order]
+
+
+@pytest.mark.parametrize("n,L,G", [(1 << 14, 2048, 85), (9001, 1024, 5), (5000, 4096, 17), (1, 2048, 85)])
+def test_candidates_equal_thresholded_plane(fd, bank, n, L, G):
+    x = synth.make_input(synth.single_small(n=max(n, 2), seed=31))[:n]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    with fd.Plan(bank, n_max=max(n, 16), seg_len=L, tpl_per_cta=G) as plan:
+        plane = plan.convolve(xd).cpu().numpy()
+        buf, count = plan.candidates(xd, threshold=THRESHOLD, max_cand=1 << 20)
+        plan.status()
+        got = _keys(fd.candidates_to_numpy(buf, count))
+    zi, ii = np.nonzero(plane > THRESHOLD)
+    assert int(count.item()) == zi.size
+    np.testing.assert_array_equal(got["tpl"], zi)                 # same set, bit-exact powers
+    np.testing.assert_array_equal(got["bin"], ii)
+    np.testing.assert_array_equal(got["power"], plane[zi, ii])
+
+
+def test_candidates_vs_oracle(fd, oracle_mod, bank):
+    x = synth.make_input(synth.single_small())
+    with fd.Plan(bank, n_max=x.size) as plan:
+        buf, count = plan.candidates(torch.from_numpy(x).cuda(), threshold=THRESHOLD)
+        plan.status()
+        got = fd.candidates_to_numpy(buf, count)
+    ref = oracle_mod.direct_power(x, bank)
+    band = TOL_FP32 * ref.max()
+    sure = np.abs(ref - THRESHOLD) > band
+    want = set(zip(*np.nonzero((ref > THRESHOLD) & sure)))
+    have = set(zip(got["tpl"].tolist(), got["bin"].tolist()))
+    assert want <= have                                            # every sure candidate found
+    extra = have - want
+    assert all(not sure[z, i] for z, i in extra)                   # the rest lie inside the band
+    assert np.max(np.abs(got["power"] - ref[got["tpl"], got["bin"]])) <= band
+    assert len(want) > 100
+
+
+def test_candidate_overflow_and_empty(fd, bank):
+    x = synth.make_input(synth.single_small(n=20000, seed=32))
+    xd = torch.from_numpy(x).cuda()
+    with fd.Plan(bank, n_max=x.size) as plan:
+        full_buf, full_count = plan.candidates(xd, max_cand=1 << 20)
+        total = int(full_count.item())
+        assert total > 50
+        buf, count = plan.candidates(xd, max_cand=10)          # counts everything, stores 10
+        assert int(count.item()) == total
+        part = fd.candidates_to_numpy(buf, count)
+        assert part.size == 10 and np.unique(part[["tpl", "bin"]]).size == 10
+        full = fd.candidates_to_numpy(full_buf, full_count)
+        assert set(zip(part["tpl"], part["bin"])) <= set(zip(full["tpl"], full["bin"]))
+        _, count0 = plan.candidates(xd, max_cand=0)             # counting only
+        assert int(count0.item()) == total
+        _, none = plan.candidates(xd, threshold=1e30)
+        assert int(none.item()) == 0
+        plan.status()
+
+
+def test_candidates_reject_tensor_core_plan(fd, bank):
+    with fd.Plan(bank, n_max=4096, precision=fd.FDAS_PREC_TC_FP16) as plan:
+        with pytest.raises(fd.FdasError) as e:
+            plan.candidates(torch.zeros(4096, dtype=torch.complex64, device="cuda"))
+        assert e.value.code == fd.fdas.FDAS_ERR_UNSUPPORTED
