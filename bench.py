@@ -319,6 +319,7 @@ def run_fdas(args):
         torch.cuda.empty_cache()
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
                  "library_unfused_ols": bench_library_ols(h, dev, xd),
+                 "length_sweep": bench_length_sweep(fd, dev, xd),
                  "batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
 
     clock_summary = clocks.summary()
@@ -445,6 +446,31 @@ def bench_library_ols(h, dev, xd, reps=5, seg_len=2048):
     torch.cuda.empty_cache()
     return {"what": "torch.fft (cuFFT) unfused overlap-save, 128 segments per step, same array and templates",
             "ms_per_array": ms, "arrays_per_s": 1e3 / ms}
+
+
+def bench_length_sweep(fd, dev, xd, lengths=(64, 128, 256, 421)):
+    """Latency against filter length (the paper's experiment, Sec. 6): 85 seeded random
+    unit-energy templates of K taps on the SKA-sized array, overlap-save (L = 2048, G = 85)
+    against the time-domain form (Eq. 1 term by term)."""
+    import torch
+    n = xd.numel()
+    out = torch.empty((85, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for K in lengths:
+        rng = np.random.default_rng(5000 + K)
+        hk = ((rng.standard_normal((85, K)) + 1j * rng.standard_normal((85, K))) / np.sqrt(2 * K)).astype(np.complex64)
+        with fd.Plan(hk, n_max=n) as plan:
+            plan.convolve(xd, out, stream)
+            ms_fd = _events_ms(lambda: plan.convolve(xd, out, stream), 10, stream)
+            plan.convolve_direct(xd, out, stream)
+            ms_td = _events_ms(lambda: plan.convolve_direct(xd, out, stream), 3, stream)
+            plan.status(stream)
+        rows.append({"K": K, "ols_ms": ms_fd, "td_ms": ms_td, "td_over_ols": ms_td / ms_fd,
+                     "td_tflops": 8.0 * n * K * 85 / (ms_td / 1e3) / 1e12})
+    del out
+    torch.cuda.empty_cache()
+    return {"workload": "N=2^22, 85 random templates of K taps", "rows": rows}
 
 
 def bench_batch(fd, h, dev, reps=10):

@@ -113,6 +113,15 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *desc);
 int fdas_convolve(fdas_plan p, const void *in_c64_dev, int64_t n, float *out_power_dev,
                   void *stream);
 
+/*
+ * fdas_convolve_direct -- the same plane by the time-domain form: Eq. (1) evaluated term
+ * by term (8NK operations per template, Table 1 "TD naive") on the CUDA cores, then |y|^2.
+ * For the filter-length comparison with overlap-save (Sec. 6, latency against filter
+ * length); arguments, layout and errors as fdas_convolve.  Asynchronous.
+ */
+int fdas_convolve_direct(fdas_plan p, const void *in_c64_dev, int64_t n, float *out_power_dev,
+                         void *stream);
+
 /* One threshold crossing of the power plane. */
 typedef struct {
     int32_t tpl;     /* template (row) index */

@@ -101,6 +101,7 @@ struct fdas_plan_s {
     double2 *d_tw64 = nullptr;  // [L] FP64 twiddles
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
     unsigned char *d_wtc = nullptr;   // tensor-core form: real 32x32 DFT matrices (hi/lo fp16)
+    float2 *d_h32 = nullptr;          // raw templates [M][K] (time-domain form)
     int *d_status = nullptr;
     int64_t device_bytes = 0;
     // batched form: the resolved persistent kernel and the plan's own lane
@@ -129,6 +130,7 @@ void plan_free(fdas_plan p)
     cudaFree(p->d_tw64);
     cudaFree(p->d_H);
     cudaFree(p->d_wtc);
+    cudaFree(p->d_h32);
     cudaFree(p->d_status);
     cudaFree(p->d_in_stage);
     cudaFree(p->d_out_stage);
@@ -563,10 +565,10 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     }
     if (rc == FDAS_OK && o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
     if (rc == FDAS_OK) rc = build_templates(p, d_h32, p->L);
-    cudaFree(d_h32);
+    p->d_h32 = d_h32;   // kept for the time-domain form
     if (rc != FDAS_OK) return cleanup_fail(rc);
     p->device_bytes = (int64_t)(sizeof(float2) * p->L + sizeof(double2) * p->L +
-                                sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) +
+                                sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) + h_bytes +
                                 (p->d_wtc ? fdas::tc_matrix_bytes() : 0));
     *out = p;
     return FDAS_OK;
@@ -611,6 +613,18 @@ int fdas_convolve(fdas_plan p, const void *in, int64_t n, float *out, void *stre
     CUtensorMap map;
     if ((rc = encode_input_map(&map, in, n))) return rc;
     return enqueue_segments(p, &map, n, out, 0, n_segments(p, n), (cudaStream_t)stream);
+}
+
+int fdas_convolve_direct(fdas_plan p, const void *in, int64_t n, float *out, void *stream)
+{
+    int rc = validate_convolve(p, in, n, out);
+    if (rc) return rc;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(FDAS_ERR_CUDA, "cannot select plan device %d", p->device);
+    cudaError_t e = fdas::launch_td_direct(static_cast<const float2 *>(in), n, p->d_h32, p->M, p->K_user, out,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "time-domain kernel launch");
+    return FDAS_OK;
 }
 
 int fdas_convolve_candidates(fdas_plan p, const void *in, int64_t n, float threshold, fdas_candidate *cand,

@@ -123,6 +123,9 @@ size_t tc_matrix_bytes();
 cudaError_t launch_ols_tc(const CUtensorMap *tmap, const OlsArgs &a, const unsigned char *wmat, int nseg,
                           cudaStream_t s);
 
+// Time-domain form (Eq. 1 term by term) over the raw templates h [M][K].
+cudaError_t launch_td_direct(const float2 *x, int64_t n, const float2 *h, int M, int K, float *out, cudaStream_t s);
+
 // Plan-time kernels (FP64).
 cudaError_t launch_twiddles(int L, double2 *w64, float2 *w32, cudaStream_t s);
 cudaError_t launch_pretransform(int L, const float2 *h32, int M, int K, const double2 *w64,

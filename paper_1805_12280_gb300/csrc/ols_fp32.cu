@@ -43,6 +43,9 @@ struct Smem {
     static constexpr size_t total = 128 + seg_bytes + e2_bytes + 2 * h_bytes + 3 * 8;
 };
 
+constexpr int kCandCap = 1024;   // candidates staged per block before one global reservation
+constexpr size_t kCandSmem = sizeof(fdas_candidate) * kCandCap + 16;
+
 template <int L>
 constexpr int minb()
 {
@@ -56,6 +59,8 @@ struct Block {
     float2 *e2;      // exchange buffer 2 [16][NT + 1]
     float4 *hb;      // template double buffer [2][8][NT]
     uint64_t *bar;   // [0] segment, [1], [2] template buffers
+    fdas_candidate *sb = nullptr;   // candidate staging [kCandCap] (candidate kernel only)
+    unsigned *sc = nullptr;         // staging reservation counter
     uint32_t seg_uses = 0, h_uses0 = 0, h_uses1 = 0;   // completed phases per barrier (scalars:
                                                        // a runtime-indexed array would spill to local memory)
 
@@ -216,27 +221,30 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
         dft<16, 1>(v);
         // ---- discard the first K-1 points, power, store the valid ones
         if constexpr (CAND) {
-            // threshold crossings instead of the plane: one atomic per warp and slot
-            const int lane = tid & 31;
+            // threshold crossings instead of the plane, staged per block in shared memory
+            float pw[16], pmax = 0.f;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int o = j * NT + obase;
-                const float pw = cabs2(v[j]);
-                const bool hit = (unsigned)o < nvalid && pw > a.threshold;
-                const unsigned mask = __ballot_sync(0xffffffffu, hit);
-                if (mask) {
-                    const int leader = __ffs(mask) - 1;
-                    unsigned long long base = 0;
-                    if (lane == leader) base = atomicAdd(a.cand_count, (unsigned long long)__popc(mask));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (hit) {
-                        const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
-                        if (idx < (unsigned long long)a.cand_max) {
-                            fdas_candidate c;
-                            c.tpl = z;
-                            c.power = pw;
-                            c.bin = seg_out + o;
-                            a.cand[idx] = c;
+                pw[j] = cabs2(v[j]);
+                pmax = fmaxf(pmax, pw[j]);
+            }
+            // only lanes holding a crossing take the append path (one shared-memory atomic per
+            // crossing); the short path keeps the warps of a block in step between barriers
+            if (pmax > a.threshold) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {     // static slots: pw stays in registers
+                    const int o = j * NT + obase;
+                    if ((unsigned)o < nvalid && pw[j] > a.threshold) {
+                        fdas_candidate c;
+                        c.tpl = z;
+                        c.power = pw[j];
+                        c.bin = seg_out + o;
+                        const unsigned idx = atomicAdd(B.sc, 1u);
+                        if (idx < (unsigned)kCandCap) {
+                            B.sb[idx] = c;
+                        } else {   // the block's staging is full: straight to global memory
+                            const unsigned long long g = atomicAdd(a.cand_count, 1ull);
+                            if (g < (unsigned long long)a.cand_max) a.cand[g] = c;
                         }
                     }
                 }
@@ -250,6 +258,17 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
             }
         }
     }
+    if constexpr (CAND) {   // one global reservation for the block's staged candidates
+        __shared__ unsigned long long flush_base;
+        __syncthreads();
+        const unsigned staged = min(*B.sc, (unsigned)kCandCap);
+        if (tid == 0) flush_base = staged ? atomicAdd(a.cand_count, (unsigned long long)staged) : 0ull;
+        __syncthreads();
+        for (unsigned i = tid; i < staged; i += NT)
+            if (flush_base + i < (unsigned long long)a.cand_max) a.cand[flush_base + i] = B.sb[i];
+        __syncthreads();
+        if (tid == 0) *B.sc = 0;
+    }
     return true;
 }
 
@@ -261,8 +280,13 @@ __global__ void __launch_bounds__(L / 16, MINB)
 {
     extern __shared__ unsigned char smem_raw[];
     Block<L> B(smem_raw);
+    if constexpr (CAND) {
+        B.sb = reinterpret_cast<fdas_candidate *>(smem_raw + Smem<L>::total);
+        B.sc = reinterpret_cast<unsigned *>(B.sb + kCandCap);
+        if (threadIdx.x == 0) *B.sc = 0;
+    }
     float2 tw1[16], tw2[16];
-    init_block<L>(B, a, tw1, tw2);
+    init_block<L>(B, a, tw1, tw2);   // its barrier also publishes *B.sc = 0
     const int z0 = blockIdx.y * a.G;
     run_item<L, CAND>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out, tw1, tw2);
 }
@@ -299,13 +323,13 @@ __global__ void __launch_bounds__(L / 16, MINB)
 }
 
 template <int L>
-static cudaError_t set_smem_attr(const void *fn, bool *done)
+static cudaError_t set_smem_attr(const void *fn, bool *done, size_t bytes = Smem<L>::total)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<L>::total);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }
@@ -314,11 +338,12 @@ template <int L, bool CAND>
 static cudaError_t launch_lc(const CUtensorMap *tmap, const OlsArgs &a, int nseg, cudaStream_t s)
 {
     auto kern = ols_fp32_kernel<L, minb<L>(), CAND>;
+    constexpr size_t smem = Smem<L>::total + (CAND ? kCandSmem : 0);
     static bool done[64] = {};
-    cudaError_t e = set_smem_attr<L>((const void *)kern, done);
+    cudaError_t e = set_smem_attr<L>((const void *)kern, done, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(nseg, (a.M + a.G - 1) / a.G);
-    kern<<<grid, L / 16, Smem<L>::total, s>>>(*tmap, a);
+    kern<<<grid, L / 16, smem, s>>>(*tmap, a);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "fdas_convolve_host": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_batch": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_convolve_candidates": (_I, [_P, _P, _I64, ctypes.c_float, _P, _I64, _P, _P]),
+    "fdas_convolve_direct": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_batch_noalloc": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_plan_status": (_I, [_P, _P]),
     "fdas_server_create": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(fdas_server_opts)]),
@@ -150,6 +151,10 @@ def fdas_convolve(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0)
 
 def fdas_convolve_host(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
     _check(load().fdas_convolve_host(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_convolve_host")
+
+
+def fdas_convolve_direct(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().fdas_convolve_direct(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_convolve_direct")
 
 
 def fdas_convolve_candidates(plan: int, in_ptr: int, n: int, threshold: float, cand_ptr: int, max_cand: int,
@@ -263,6 +268,17 @@ class Plan:
         if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != self.n_templates * n:
             raise ValueError("out must be a contiguous float32 tensor with M*n elements")
         fdas_convolve(self.handle, x.data_ptr(), n, out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def convolve_direct(self, x, out=None, stream=None):
+        """The same plane by the time-domain form (Eq. 1 term by term)."""
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        n = x.numel()
+        if out is None:
+            out = torch.empty((self.n_templates, n), dtype=torch.float32, device=x.device)
+        fdas_convolve_direct(self.handle, x.data_ptr(), n, out.data_ptr(), _stream_handle(stream))
         return out
 
     def candidates(self, x, threshold: float = 7.0, max_cand: int = 1 << 20, stream=None, buf=None, count=None):

@@ -88,3 +88,22 @@ def test_candidates_reject_tensor_core_plan(fd, bank):
         with pytest.raises(fd.FdasError) as e:
             plan.candidates(torch.zeros(4096, dtype=torch.complex64, device="cuda"))
         assert e.value.code == fd.fdas.FDAS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("threshold", [0.5, -1.0])
+def test_candidates_past_the_block_staging(fd, bank, threshold):
+    # low thresholds put more than the 1024 staged slots of a block into the list: the rest
+    # goes straight to global memory; T < 0 selects every output of the plane
+    n = 20000
+    x = synth.make_input(synth.single_small(n=n, seed=33))
+    xd = torch.from_numpy(x).cuda()
+    with fd.Plan(bank, n_max=n) as plan:
+        plane = plan.convolve(xd).cpu().numpy()
+        buf, count = plan.candidates(xd, threshold=threshold, max_cand=85 * n + 16)
+        plan.status()
+        got = _keys(fd.candidates_to_numpy(buf, count))
+    zi, ii = np.nonzero(plane > threshold)
+    assert int(count.item()) == zi.size and (threshold > 0 or zi.size == 85 * n)
+    np.testing.assert_array_equal(got["tpl"], zi)
+    np.testing.assert_array_equal(got["bin"], ii)
+    np.testing.assert_array_equal(got["power"], plane[zi, ii])
