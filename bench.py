@@ -319,6 +319,7 @@ def run_fdas(args):
         torch.cuda.empty_cache()
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
                  "library_unfused_ols": bench_library_ols(h, dev, xd),
+                 "library_full_fdfir": bench_library_fdfir(h, dev, xd),
                  "length_sweep": bench_length_sweep(fd, dev, xd),
                  "batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
 
@@ -446,6 +447,33 @@ def bench_library_ols(h, dev, xd, reps=5, seg_len=2048):
     torch.cuda.empty_cache()
     return {"what": "torch.fft (cuFFT) unfused overlap-save, 128 segments per step, same array and templates",
             "ms_per_array": ms, "arrays_per_s": 1e3 / ms}
+
+
+def library_full_fdfir(x, h, t_chunk=5):
+    """The paper's naive FDFIR (Eq. 2) over the whole array: y = IFFT(FFT(x) . FFT(h)) with
+    transforms of length 2^ceil(log2(N + K - 1)) (no segmentation), |y|^2 of the first N
+    outputs; torch.fft (cuFFT on a device tensor), templates `t_chunk` at a time."""
+    import torch
+    n, (m, k) = x.numel(), h.shape
+    nfft = 1 << int(np.ceil(np.log2(n + k - 1)))
+    X = torch.fft.fft(x, n=nfft)
+    out = torch.empty((m, n), dtype=torch.float32, device=x.device)
+    for z0 in range(0, m, t_chunk):
+        Hz = torch.fft.fft(h[z0:z0 + t_chunk], n=nfft)
+        out[z0:z0 + t_chunk] = torch.fft.ifft(X[None, :] * Hz)[:, :n].abs().square()
+    return out
+
+
+def bench_library_fdfir(h, dev, xd, reps=3):
+    """Same-GPU library comparison (not the product path): naive full-length FDFIR."""
+    import torch
+    hd = torch.from_numpy(h).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    library_full_fdfir(xd, hd)
+    ms = _events_ms(lambda: library_full_fdfir(xd, hd), reps, stream)
+    torch.cuda.empty_cache()
+    return {"what": "torch.fft (cuFFT) naive FDFIR: 2^23-point transforms of the whole array per template, "
+                    "same array and templates", "ms_per_array": ms, "arrays_per_s": 1e3 / ms}
 
 
 def bench_length_sweep(fd, dev, xd, lengths=(64, 128, 256, 421)):
