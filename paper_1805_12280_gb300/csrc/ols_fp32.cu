@@ -21,27 +21,47 @@
 #include "fft_regs.cuh"
 #include "ols_common.cuh"
 #include "ptx.cuh"
+#include "tmem.cuh"
 
 // Minimum resident blocks per SM requested from the compiler (caps registers per thread).
 #ifndef FDAS_MINB_1024
 #define FDAS_MINB_1024 4
 #endif
 #ifndef FDAS_MINB_2048
-#define FDAS_MINB_2048 2
+#define FDAS_MINB_2048 4
 #endif
 #ifndef FDAS_MINB_4096
-#define FDAS_MINB_4096 1
+#define FDAS_MINB_4096 2
+#endif
+
+// Template buffers per block: 2 prefetches two templates ahead; 1 prefetches one ahead and
+// frees L*8 bytes of shared memory (one more resident block per SM at L = 2048 and 4096).
+#ifndef FDAS_HBUF_2048
+#define FDAS_HBUF_2048 1
+#endif
+#ifndef FDAS_HBUF_4096
+#define FDAS_HBUF_4096 1
 #endif
 
 namespace fdas {
+
+template <int L>
+__host__ __device__ constexpr int hbuf() { return L == 2048 ? FDAS_HBUF_2048 : (L == 4096 ? FDAS_HBUF_4096 : 2); }
 
 template <int L>
 struct Smem {
     static constexpr size_t seg_bytes = sizeof(float2) * L;                   // segment / exchange 1
     static constexpr size_t e2_bytes = sizeof(float2) * 16 * Geo<L>::LD2;    // exchange 2
     static constexpr size_t h_bytes = sizeof(float2) * L;                     // one pre-transformed template
-    static constexpr size_t total = 128 + seg_bytes + e2_bytes + 2 * h_bytes + 3 * 8;
+    static constexpr size_t total = 128 + seg_bytes + e2_bytes + hbuf<L>() * h_bytes + 3 * 8 + 8;   // + TMEM slot
 };
+
+// Tensor memory per block: each thread keeps its inverse twiddles (2 x 32 columns) and the
+// segment spectrum (32 columns) in its own TMEM lane instead of registers; threads of the
+// second warpgroup (L = 4096) use columns 96.. of the same lanes.
+template <int L>
+constexpr uint32_t kTmemCols = (L / 16 > 128) ? 256u : 128u;
+constexpr uint32_t kColTw1 = 0, kColTw2 = 32, kColX = 64, kColGroup = 96;
 
 constexpr int kCandCap = 1024;   // candidates staged per block before one global reservation
 constexpr size_t kCandSmem = sizeof(fdas_candidate) * kCandCap + 16;
@@ -59,6 +79,8 @@ struct Block {
     float2 *e2;      // exchange buffer 2 [16][NT + 1]
     float4 *hb;      // template double buffer [2][8][NT]
     uint64_t *bar;   // [0] segment, [1], [2] template buffers
+    uint32_t *tslot; // TMEM base address written by the allocating warp
+    uint32_t tmem = 0;
     fdas_candidate *sb = nullptr;   // candidate staging [kCandCap] (candidate kernel only)
     unsigned *sc = nullptr;         // staging reservation counter
     uint32_t seg_uses = 0, h_uses0 = 0, h_uses1 = 0;   // completed phases per barrier (scalars:
@@ -69,12 +91,13 @@ struct Block {
         e1 = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
         e2 = e1 + L;
         hb = reinterpret_cast<float4 *>(e2 + 16 * Geo<L>::LD2);
-        bar = reinterpret_cast<uint64_t *>(hb + 2 * 8 * Geo<L>::NT);
+        bar = reinterpret_cast<uint64_t *>(hb + hbuf<L>() * 8 * Geo<L>::NT);
+        tslot = reinterpret_cast<uint32_t *>(bar + 3);
     }
 };
 
 template <int L>
-__device__ __forceinline__ void init_block(Block<L> &B, const OlsArgs &a, float2 (&tw1)[16], float2 (&tw2)[16])
+__device__ __forceinline__ void init_block(Block<L> &B, const OlsArgs &a)
 {
     using Gm = Geo<L>;
     constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, MASK = L - 1;
@@ -85,7 +108,13 @@ __device__ __forceinline__ void init_block(Block<L> &B, const OlsArgs &a, float2
         mbar_init(&B.bar[2], 1);
         fence_mbar_init();
     }
+    if ((tid >> 5) == 0) tmem_alloc(B.tslot, kTmemCols<L>);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    B.tmem = *B.tslot;
     // Inverse-transform twiddles, fixed for this thread across all items and templates.
+    float2 tw1[16], tw2[16];
 #pragma unroll
     for (int g = 0; g < GC; ++g) {
         const int k2 = hi + (NT / 16) * g;
@@ -98,7 +127,20 @@ __device__ __forceinline__ void init_block(Block<L> &B, const OlsArgs &a, float2
 #pragma unroll
         for (int b = 0; b < Q; ++b) tw2[g * Q + b] = cconj(__ldg(&a.tw[((b * R + cg) * k1) & MASK]));
     }
+    const uint32_t my = tmem_lane_addr(B.tmem, (uint32_t)(tid >> 7) * kColGroup);
+    tmem_st_c16(my + kColTw1, tw1);
+    tmem_st_c16(my + kColTw2, tw2);
     __syncthreads();
+}
+
+// Every thread of the block, after its last TMEM access: the allocating warp frees it.
+template <int L>
+__device__ __forceinline__ void release_block(Block<L> &B)
+{
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(B.tmem, kTmemCols<L>);
 }
 
 // After a timed-out wait: give each copy that may still be in flight a bounded time to
@@ -115,13 +157,13 @@ __device__ __noinline__ void drain(uint64_t *bar, unsigned pending, unsigned par
 // if a bounded wait ran out; the status bit is then set.
 template <int L, bool CAND = false>
 __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CUtensorMap *map, int seg, int z0,
-                                         int z1, int64_t n, float *out, const float2 (&tw1)[16],
-                                         const float2 (&tw2)[16])
+                                         int z1, int64_t n, float *out)
 {
     using Gm = Geo<L>;
     constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
     constexpr int MASK = L - 1;
     constexpr uint32_t HBYTES = (uint32_t)Smem<L>::h_bytes;
+    constexpr int NHB = hbuf<L>();
     float2 *e1 = B.e1, *e2 = B.e2;
     float4 *hb = B.hb;
     uint64_t *bar = B.bar;
@@ -133,7 +175,7 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
         const int c0 = seg * a.S - (a.K - 1);
 #pragma unroll
         for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, map, c0 + 256 * j, &bar[0]);
-        for (int i = 0; i < 2 && z0 + i < z1; ++i) {
+        for (int i = 0; i < NHB && z0 + i < z1; ++i) {
             mbar_arrive_expect_tx(&bar[1 + i], HBYTES);
             bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, HBYTES, &bar[1 + i]);
         }
@@ -144,15 +186,20 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     if (!__syncthreads_and(seg_ok)) {
         if (tid == 0) {
             atomicOr(a.status, STATUS_WAIT_TIMEOUT);
-            const unsigned pending = 1u | 2u | (z0 + 1 < z1 ? 4u : 0u);
+            const unsigned pending = 1u | 2u | (NHB == 2 && z0 + 1 < z1 ? 4u : 0u);
             const unsigned parity = ((B.seg_uses - 1) & 1u) | ((B.h_uses0 & 1u) << 1) | ((B.h_uses1 & 1u) << 2);
             drain(bar, pending, parity);
         }
         return false;
     }
 
-    float2 v[16], X[16];
-    forward_fft<L>(e1, e2, a.tw, v, X);
+    float2 v[16];
+    const uint32_t my = tmem_lane_addr(B.tmem, (uint32_t)(tid >> 7) * kColGroup);
+    {
+        float2 X[16];
+        forward_fft<L>(e1, e2, a.tw, v, X);
+        tmem_st_c16(my + kColX, X);   // the spectrum waits in TMEM for the template loop
+    }
     __syncthreads();   // every thread has read e1 before the template loop rewrites it
 
     const int64_t seg_out = (int64_t)seg * a.S;                 // first output index of this segment
@@ -161,21 +208,24 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     const int obase = tid - (a.K - 1);                          // output index of register slot 0
 
     for (int z = z0; z < z1; ++z) {
-        const int buf = (z - z0) & 1;
+        const int buf = NHB == 2 ? ((z - z0) & 1) : 0;
         const float4 *hz = hb + buf * 8 * NT;
         const uint32_t hu = buf ? B.h_uses1 : B.h_uses0;
         const bool h_ok = mbar_wait_bounded(&bar[1 + buf], hu & 1, kWaitLimitNs);
         if (buf) B.h_uses1++; else B.h_uses0++;
         // ---- element-wise product with H_z (1/L folded in)
+        tmem_ld_c16(my + kColX, v);
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
             const float4 h = hz[jp * NT + tid];
-            v[2 * jp] = cmul(X[2 * jp], make_float2(h.x, h.y));
-            v[2 * jp + 1] = cmul(X[2 * jp + 1], make_float2(h.z, h.w));
+            v[2 * jp] = cmul(v[2 * jp], make_float2(h.x, h.y));
+            v[2 * jp + 1] = cmul(v[2 * jp + 1], make_float2(h.z, h.w));
         }
         // ---- inverse pass C': R-point IDFT over k3, twiddle conj W_{QR}^{c k2}
         dft<R, 1, 1, 0>(v);
         if constexpr (GC == 2) dft<R, 1, 1, R>(v);
+        float2 tw1[16];
+        tmem_ld_c16(my + kColTw1, tw1);
 #pragma unroll
         for (int g = 0; g < GC; ++g) {
             const int k2 = hi + (NT / 16) * g;
@@ -187,17 +237,17 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
             if (tid == 0) {
                 atomicOr(a.status, STATUS_WAIT_TIMEOUT);
                 const int other = 1 - buf;
-                const unsigned pending = (2u << buf) | (z + 1 < z1 ? (2u << other) : 0u);
+                const unsigned pending = (2u << buf) | (NHB == 2 && z + 1 < z1 ? (2u << other) : 0u);
                 const uint32_t hb_ = buf ? B.h_uses1 : B.h_uses0, ho_ = buf ? B.h_uses0 : B.h_uses1;
                 const unsigned parity = (((hb_ - 1) & 1u) << (1 + buf)) | ((ho_ & 1u) << (1 + other));
                 drain(bar, pending, parity);
             }
             return false;
         }
-        // every thread has read hb[buf]: refill it with the template two ahead
-        if (tid == 0 && z + 2 < z1) {
+        // every thread has read hb[buf]: refill it with the template NHB ahead
+        if (tid == 0 && z + NHB < z1) {
             mbar_arrive_expect_tx(&bar[1 + buf], HBYTES);
-            bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + 2) * 8 * NT, HBYTES, &bar[1 + buf]);
+            bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + NHB) * 8 * NT, HBYTES, &bar[1 + buf]);
         }
         // ---- inverse pass B': Q-point IDFT over k2, twiddle conj W_L^{(bR + c) k1}
 #pragma unroll
@@ -208,6 +258,8 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
         }
         dft<Q, 1, 1, 0>(v);
         if constexpr (GB == 2) dft<Q, 1, 1, Q>(v);
+        float2 tw2[16];
+        tmem_ld_c16(my + kColTw2, tw2);
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
             const int cg = hi + (NT / 16) * g;
@@ -285,10 +337,10 @@ __global__ void __launch_bounds__(L / 16, MINB)
         B.sc = reinterpret_cast<unsigned *>(B.sb + kCandCap);
         if (threadIdx.x == 0) *B.sc = 0;
     }
-    float2 tw1[16], tw2[16];
-    init_block<L>(B, a, tw1, tw2);   // its barrier also publishes *B.sc = 0
+    init_block<L>(B, a);   // its barriers also publish *B.sc = 0
     const int z0 = blockIdx.y * a.G;
-    run_item<L, CAND>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out, tw1, tw2);
+    run_item<L, CAND>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out);
+    release_block<L>(B);
 }
 
 // Persistent: resident blocks take items (array, group, segment) from *counter until the
@@ -301,8 +353,7 @@ __global__ void __launch_bounds__(L / 16, MINB)
     extern __shared__ unsigned char smem_raw[];
     __shared__ int item_sh;
     Block<L> B(smem_raw);
-    float2 tw1[16], tw2[16];
-    init_block<L>(B, a, tw1, tw2);
+    init_block<L>(B, a);
     for (;;) {
         __syncthreads();                       // the previous item is finished by every thread
         if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
@@ -318,8 +369,9 @@ __global__ void __launch_bounds__(L / 16, MINB)
         const int64_t local = item - ar.item_off;
         const int g = (int)(local / ar.nseg), seg = (int)(local % ar.nseg);
         const int z0 = g * a.G;
-        if (!run_item<L>(B, a, &ar.map, seg, z0, min(z0 + a.G, a.M), ar.n, ar.out, tw1, tw2)) return;
+        if (!run_item<L>(B, a, &ar.map, seg, z0, min(z0 + a.G, a.M), ar.n, ar.out)) break;
     }
+    release_block<L>(B);
 }
 
 template <int L>
