@@ -17,6 +17,7 @@
 #include "fft_regs.cuh"
 #include "ols_common.cuh"
 #include "ptx.cuh"
+#include "tmem.cuh"
 
 namespace fdas {
 
@@ -31,7 +32,9 @@ constexpr uint32_t A_BYTES = 16 * A_SBO;                // 10240
 constexpr uint32_t B_LBO = 128, B_SBO = 512, B_BYTES = 4 * B_SBO;   // 2048 per matrix
 constexpr uint32_t W_BYTES = 4 * B_BYTES;               // B' hi, B' lo, A' hi, A' lo
 constexpr uint32_t H_BYTES = sizeof(float2) * L;
-constexpr uint32_t TMEM_COLS = 64;                      // D of B' (32) and of A' (32)
+// TMEM columns: D of B' [0, 32), D of A' [32, 64), this thread's segment spectrum [64, 96)
+// and C' twiddles [96, 128) (kept there instead of registers).
+constexpr uint32_t TMEM_COLS = 128, COL_DB = 0, COL_DA = 32, COL_X = 64, COL_TW1 = 96;
 // kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
 constexpr uint32_t IDESC = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
@@ -78,19 +81,11 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive fp32 columns of this thread's TMEM lane (warp w reads lanes 32w..32w+31).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&f)[32])
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld_f32(uint32_t taddr, float (&f)[32])
 {
     uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tmem_ld32(taddr, r);
 #pragma unroll
     for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
 }
@@ -126,7 +121,7 @@ __global__ void tc_matrix_kernel(unsigned char *out)
 }  // namespace tc
 
 #ifndef FDAS_TC_MINB
-#define FDAS_TC_MINB 1
+#define FDAS_TC_MINB 3
 #endif
 __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     ols_tc_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a, const unsigned char *__restrict__ wmat)
@@ -172,13 +167,19 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
             bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, H_BYTES, &bar[1 + i]);
         }
     }
-    // Inverse twiddles: C' output (W_{QR}^{-c k2}) and B' output (W_L^{-(bR + c) k1}).
-    float2 tw1[16], tw2[16];
+    // Inverse twiddles: C' output (W_{QR}^{-c k2}, parked in TMEM) and B' output
+    // (W_L^{-(bR + c) k1}, registers).
+    const uint32_t my = tmem + ((uint32_t)(warp * 32) << 16);
+    float2 tw2[16];
+    {
+        float2 tw1[16];
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        const int k2 = hi + 8 * g;
+        for (int g = 0; g < 2; ++g) {
+            const int k2 = hi + 8 * g;
 #pragma unroll
-        for (int c = 0; c < R; ++c) tw1[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & (L - 1)]));
+            for (int c = 0; c < R; ++c) tw1[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & (L - 1)]));
+        }
+        tmem_st_c16(my + COL_TW1, tw1);
     }
 #pragma unroll
     for (int b = 0; b < Q; ++b) tw2[b] = cconj(__ldg(&a.tw[((b * R + hi) * k1) & (L - 1)]));
@@ -188,9 +189,11 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     // per-buffer counters as scalars (a runtime-indexed array would live in local memory)
     uint32_t h_uses0 = 0, h_uses1 = 0, h_iss0 = z0 < z1, h_iss1 = z0 + 1 < z1;
     uint32_t b_uses = 0, b_done = 0, a_uses = 0, a_done = 0;   // MMA completions awaited / seen
-    float2 v[16], X[16];
+    float2 v[16];
     if (ok) {
+        float2 X[16];
         forward_fft<L>(e1, e2, a.tw, v, X);
+        tmem_st_c16(my + COL_X, X);   // the spectrum waits in TMEM for the template loop
         __syncthreads();   // e1/e2 are free: they become the A operands
     }
     const int64_t seg_out = (int64_t)seg * a.S;
@@ -203,21 +206,23 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     // finish template z-1 (A' output, power, stores); the A' MMA of template z runs while
     // they prepare template z+1 (product, C', B' operand).
     float f[32];
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     for (int z = z0; ok && z < z1; ++z) {
         const int buf = (z - z0) & 1;
         const float4 *hz = hb + buf * 8 * NT;
         const bool h_ok = mbar_wait_bounded(&bar[1 + buf], (buf ? h_uses1 : h_uses0) & 1, kWaitLimitNs);
         if (buf) h_uses1++; else h_uses0++;
         // ---- S1(z): product with H_z, pass C' (radix 8, CUDA cores), twiddle, fp16 rows of B'
+        tmem_ld_c16(my + COL_X, v);
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
             const float4 h = hz[jp * NT + tid];
-            v[2 * jp] = cmul(X[2 * jp], make_float2(h.x, h.y));
-            v[2 * jp + 1] = cmul(X[2 * jp + 1], make_float2(h.z, h.w));
+            v[2 * jp] = cmul(v[2 * jp], make_float2(h.x, h.y));
+            v[2 * jp + 1] = cmul(v[2 * jp + 1], make_float2(h.z, h.w));
         }
         dft<R, 1, 1, 0>(v);
         dft<R, 1, 1, R>(v);
+        float2 tw1[16];
+        tmem_ld_c16(my + COL_TW1, tw1);
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             const int k2 = hi + 8 * g;
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
             a_uses++;
             a_done += ma_ok;
             fence_after_sync();
-            tmem_ld32(tmem + lane_base + 32, f);
+            tmem_ld_f32(my + COL_DA, f);
             float *orow = a.out + (size_t)(z - 1) * (size_t)a.n + seg_out;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
         b_uses++;
         b_done += mb_ok;
         fence_after_sync();
-        tmem_ld32(tmem + lane_base, f);
+        tmem_ld_f32(my + COL_DB, f);
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             const float2 y = cmul(make_float2(f[2 * b], f[2 * b + 1]), tw2[b]);
@@ -288,8 +293,8 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 const uint64_t ad = smem_desc(aA_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
-                mma_f16(tmem + 32, ad, smem_desc(w_addr + 2 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
-                mma_f16(tmem + 32, ad, smem_desc(w_addr + 3 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
+                mma_f16(tmem + COL_DA, ad, smem_desc(w_addr + 2 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
+                mma_f16(tmem + COL_DA, ad, smem_desc(w_addr + 3 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
             }
             mma_commit(&bar[4]);
         }
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
         a_uses++;
         a_done += ma_ok;
         fence_after_sync();
-        tmem_ld32(tmem + lane_base + 32, f);
+        tmem_ld_f32(my + COL_DA, f);
         float *orow = a.out + (size_t)(z1 - 1) * (size_t)a.n + seg_out;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
