@@ -72,6 +72,7 @@ typedef struct {
     int64_t device_bytes; /* device memory owned by the plan */
     int     tuned;        /* 1 if the autotuner chose seg_len and tpl_per_cta */
     float   tune_ms[9];   /* autotuner: ms per plane of its tuning array, [L in 1024, 2048, 4096][G in 5, 17, 85] (0 = not run) */
+    int     batch_blocks; /* blocks of the persistent batch kernel (resident blocks per SM x SMs) */
 } fdas_plan_desc;
 
 /*

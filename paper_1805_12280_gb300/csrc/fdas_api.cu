@@ -589,6 +589,7 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *d)
     d->device_bytes = p->device_bytes;
     d->tuned = p->tuned;
     for (int i = 0; i < 9; ++i) d->tune_ms[i] = p->tune_ms[i / 3][i % 3];
+    d->batch_blocks = p->bk.resident;
     return FDAS_OK;
 }
 

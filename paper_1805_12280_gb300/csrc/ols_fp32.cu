@@ -72,6 +72,16 @@ constexpr int minb()
     return L == 4096 ? FDAS_MINB_4096 : (L == 2048 ? FDAS_MINB_2048 : FDAS_MINB_1024);
 }
 
+// The persistent batch kernel carries its item loop in registers too: its own bound.
+#ifndef FDAS_BATCH_MINB_2048
+#define FDAS_BATCH_MINB_2048 4
+#endif
+template <int L>
+constexpr int batch_minb()
+{
+    return L == 2048 ? FDAS_BATCH_MINB_2048 : minb<L>();
+}
+
 // Shared-memory carve-up and mbarrier phase bookkeeping of one block.
 template <int L>
 struct Block {
@@ -382,6 +392,10 @@ static cudaError_t set_smem_attr(const void *fn, bool *done, size_t bytes = Smem
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // prefer the largest shared-memory carveout: the occupancy query (and the persistent
+    // grid sized from it) otherwise assumes a smaller one
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }
@@ -415,22 +429,39 @@ cudaError_t launch_ols_fp32(int L, const CUtensorMap *tmap, const OlsArgs &a, in
     }
 }
 
+// Blocks per SM from the kernel's own resource use (registers, shared memory, threads and
+// TMEM columns).  The persistent kernel's blocks never wait for one another, so a grid larger
+// than what fits at once is still correct; the count only has to fill the GPU.
 template <int L>
 static cudaError_t batch_kernel_l(BatchKernel *k)
 {
-    auto kern = ols_fp32_batch<L, minb<L>()>;
+    auto kern = ols_fp32_batch<L, batch_minb<L>()>;
     static bool done[64] = {};
     cudaError_t e = set_smem_attr<L>((const void *)kern, done);
     if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L / 16, Smem<L>::total)) != cudaSuccess)
-        return e;
+    cudaFuncAttributes fa;
+    int dev = 0;
+    if ((e = cudaFuncGetAttributes(&fa, (const void *)kern)) != cudaSuccess) return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    cudaDeviceProp pr;
+    if ((e = cudaGetDeviceProperties(&pr, dev)) != cudaSuccess) return e;
+    const int threads = L / 16, warps = threads / 32;
+    const int regs_per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = pr.regsPerMultiprocessor / (warps * regs_per_warp);
+    const size_t smem_block = Smem<L>::total + fa.sharedSizeBytes + pr.reservedSharedMemPerBlock;
+    const int by_smem = (int)(pr.sharedMemPerMultiprocessor / smem_block);
+    const int by_threads = pr.maxThreadsPerMultiProcessor / threads;
+    const int by_tmem = 512 / (int)kTmemCols<L>;
+    int per_sm = by_regs;
+    per_sm = per_sm < by_smem ? per_sm : by_smem;
+    per_sm = per_sm < by_threads ? per_sm : by_threads;
+    per_sm = per_sm < by_tmem ? per_sm : by_tmem;
+    per_sm = per_sm < pr.maxBlocksPerMultiProcessor ? per_sm : pr.maxBlocksPerMultiProcessor;
+    if (per_sm < 1) per_sm = 1;
     k->fn = (const void *)kern;
-    k->block = L / 16;
+    k->block = threads;
     k->smem = Smem<L>::total;
-    k->resident = per_sm * sms;
+    k->resident = per_sm * pr.multiProcessorCount;
     return cudaSuccess;
 }
 

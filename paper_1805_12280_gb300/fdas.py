@@ -43,7 +43,8 @@ class fdas_plan_desc(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("n_templates", ctypes.c_int), ("tpl_len", ctypes.c_int),
                 ("frame_len", ctypes.c_int), ("seg_len", ctypes.c_int), ("seg_step", ctypes.c_int),
                 ("tpl_per_cta", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
-                ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9)]
+                ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9),
+                ("batch_blocks", ctypes.c_int)]
 
 
 class fdas_candidate(ctypes.Structure):

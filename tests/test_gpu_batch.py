@@ -57,6 +57,14 @@ def test_batch_more_than_one_table(fd, oracle_mod, bank):
         compare(outs[i].cpu().numpy(), oracle_mod.direct_power(x, hs), TOL_FP32)
 
 
+def test_persistent_grid_fills_the_gpu(fd, bank):
+    # the persistent kernel runs one block per resident slot: several per SM
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for L, per_sm in ((1024, 4), (2048, 4), (4096, 2)):
+        with fd.Plan(bank, n_max=1 << 16, seg_len=L) as plan:
+            assert plan.desc.batch_blocks == per_sm * sms, (L, plan.desc.batch_blocks)
+
+
 def test_batch_empty_and_invalid(fd, bank):
     with fd.Plan(bank[:3], n_max=1000) as plan:
         plan.convolve_batch([])
