@@ -49,6 +49,10 @@ def dist_env():
     return rank, world, local
 
 
+def local_index(dev) -> int:
+    return dev.index if getattr(dev, "index", None) is not None else 0
+
+
 def rank_array_spec(rank: int, log2n: int = 22):
     """Each rank processes its own dedispersion trial (replicas: no data exchange)."""
     return synth.single_ska(n=1 << log2n, seed=1 + rank)
@@ -69,6 +73,26 @@ def max_over_ranks(value: float, device=None) -> float:
 def aggregate_rate(world: int, units_per_rank: int, max_elapsed_s: float) -> float:
     """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
     return world * units_per_rank / max_elapsed_s
+
+
+def gpu_local_cpus(device_index: int):
+    """CPUs the kernel lists as local to the GPU's PCI function (None if unknown)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(device_index)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            text = f.read().strip()
+    except Exception:
+        return None
+    cpus = set()
+    for part in text.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return sorted(cpus) or None
 
 
 def measured_peaks():
@@ -274,6 +298,16 @@ def run_fdas(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
+        # host buffers on the NUMA node next to the GPU: run (and first-touch) on its local CPUs
+        local = gpu_local_cpus(local_index(dev))
+        saved_affinity = os.sched_getaffinity(0)
+        if local and set(local) & saved_affinity:
+            try:
+                os.sched_setaffinity(0, set(local) & saved_affinity)
+            except OSError:
+                local = None
+        else:
+            local = None
         xh = torch.from_numpy(x).pin_memory()
         oh = torch.empty((m, n), dtype=torch.float32).pin_memory()
         xh_np, oh_np = xh.numpy(), oh.numpy()
@@ -287,7 +321,9 @@ def run_fdas(args):
             plan.convolve_host(xh_np, oh_np)
         dt = max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": aggregate_rate(world, ks, dt), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * m * n,
-               "steps": ks, "api": "fdas_convolve_host (pinned host buffers)"}
+               "steps": ks, "api": "fdas_convolve_host (pinned host buffers)",
+               "host_cpus": f"{local[0]}-{local[-1]}" if local else "unrestricted"}
+        os.sched_setaffinity(0, saved_affinity)   # the CPU baseline uses every core again
         del xh, oh
 
     peak, peak_kind = measured_peaks()
