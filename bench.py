@@ -354,6 +354,7 @@ def run_fdas(args):
         del out
         torch.cuda.empty_cache()
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
+                 "template_groups": bench_groups(fd, h, dev, xd),
                  "library_unfused_ols": bench_library_ols(h, dev, xd),
                  "library_full_fdfir": bench_library_fdfir(h, dev, xd),
                  "length_sweep": bench_length_sweep(fd, dev, xd),
@@ -410,6 +411,26 @@ def bench_tc(fd, h, dev, xd, reps=50):
                      "hbm_frac": algorithmic_bytes(n, m) / (ms / 1e3) / 1e9 / measured_peaks()[0]}
     res["accuracy"] = ("tests/test_gpu_tc.py: max |P - P_ref| / max P_ref < 1e-3 against the FP64 oracle "
                        "(tolerance 2e-3), strong-candidate sets identical")
+    del out
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_groups(fd, h, dev, xd, reps=50):
+    """Templates grouped by support length (group_support=1): one launch per group, each with
+    its own frame and step; beside it the ungrouped plan on the same array."""
+    import torch
+    n, m = xd.numel(), h.shape[0]
+    out = torch.empty((m, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": "N=2^22, 85 templates, L=2048, G=85 (same array as the headline)"}
+    for name, grp in (("grouped", 1), ("ungrouped", 0)):
+        with fd.Plan(h, n_max=n, group_support=grp) as plan:
+            for _ in range(3):
+                plan.convolve(xd, out, stream)
+            ms = _events_ms(lambda: plan.convolve(xd, out, stream), reps, stream)
+            plan.status(stream)
+            res[name] = {"ms_per_array": ms, "arrays_per_s": 1e3 / ms, "launches": plan.desc.groups}
     del out
     torch.cuda.empty_cache()
     return res

@@ -55,6 +55,12 @@ typedef struct {
                          persistent kernel on one array of min(n_max, 2^21) points and keep the
                          fastest (seg_len is then ignored; a non-zero tpl_per_cta stays fixed);
                          results are cached per process by (device, M, K, tuning length) */
+    int group_support;/* 1: group the templates by the length of their nonzero support, each
+                         group with its own overlap-save frame and step and its templates stored
+                         shifted to their first nonzero tap (fewer inverse FFTs when supports
+                         differ); one launch per group.  FP32 form, without autotuning; used by
+                         fdas_convolve, fdas_convolve_host and fdas_convolve_candidates (the
+                         batched and served forms return FDAS_ERR_UNSUPPORTED for such a plan) */
 } fdas_opts;
 
 /* Read-only description of a plan. */
@@ -73,6 +79,7 @@ typedef struct {
     int     tuned;        /* 1 if the autotuner chose seg_len and tpl_per_cta */
     float   tune_ms[9];   /* autotuner: ms per plane of its tuning array, [L in 1024, 2048, 4096][G in 5, 17, 85] (0 = not run) */
     int     batch_blocks; /* blocks of the persistent batch kernel (resident blocks per SM x SMs) */
+    int     groups;       /* template groups = kernel launches per plane (1 unless group_support) */
 } fdas_plan_desc;
 
 /*

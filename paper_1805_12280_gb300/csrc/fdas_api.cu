@@ -12,6 +12,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "fdas_internal.cuh"
 
@@ -102,6 +103,15 @@ struct fdas_plan_s {
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
     unsigned char *d_wtc = nullptr;   // tensor-core form: real 32x32 DFT matrices (hi/lo fp16)
     float2 *d_h32 = nullptr;          // raw templates [M][K] (time-domain form)
+    // grouped plans: templates permuted into support groups, stored shifted to their first tap
+    struct Group {
+        int first, count, K, S;
+        int64_t min_shift;
+    };
+    int ngroups = 1;
+    Group groups[8] = {};
+    int *d_rows = nullptr;            // [M] plane row of permuted template r
+    int *d_shifts = nullptr;          // [M] first nonzero tap of permuted template r
     int *d_status = nullptr;
     int64_t device_bytes = 0;
     // batched form: the resolved persistent kernel and the plan's own lane
@@ -131,6 +141,8 @@ void plan_free(fdas_plan p)
     cudaFree(p->d_H);
     cudaFree(p->d_wtc);
     cudaFree(p->d_h32);
+    cudaFree(p->d_rows);
+    cudaFree(p->d_shifts);
     cudaFree(p->d_status);
     cudaFree(p->d_in_stage);
     cudaFree(p->d_out_stage);
@@ -156,8 +168,7 @@ int validate_convolve(fdas_plan p, const void *in, int64_t n, const float *out)
 
 int64_t n_segments(const fdas_plan p, int64_t n) { return (n + p->S - 1) / p->S; }
 
-int enqueue_segments(fdas_plan p, const CUtensorMap *map, int64_t n, float *out, int64_t s0, int64_t s1,
-                     cudaStream_t stream)
+fdas::OlsArgs base_args(fdas_plan p, int64_t n, float *out)
 {
     fdas::OlsArgs a;
     a.H = p->d_H;
@@ -168,14 +179,117 @@ int enqueue_segments(fdas_plan p, const CUtensorMap *map, int64_t n, float *out,
     a.G = p->G;
     a.S = p->S;
     a.K = p->K;
-    a.seg_begin = (int)s0;
+    a.seg_begin = 0;
     a.status = p->d_status;
-    cudaError_t e = p->precision == FDAS_PREC_TC_FP16 ? fdas::launch_ols_tc(map, a, p->d_wtc, (int)(s1 - s0), stream)
-                                                       : fdas::launch_ols_fp32(p->L, map, a, (int)(s1 - s0), stream);
+    return a;
+}
+
+// Launch segments [s0, s1) of an ungrouped plan (a carries the epilogue settings).
+int launch_range(fdas_plan p, const CUtensorMap *map, fdas::OlsArgs a, int64_t s0, int64_t s1, cudaStream_t stream)
+{
+    a.seg_begin = (int)s0;
+    cudaError_t e = fdas::launch_ols_fp32(p->L, map, a, (int)(s1 - s0), stream);
     if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch");
     return FDAS_OK;
 }
 
+// All segments of every template group: one launch per group.
+int launch_all(fdas_plan p, const CUtensorMap *map, const fdas::OlsArgs &a0, int64_t n, cudaStream_t stream)
+{
+    if (p->ngroups <= 1 && !p->d_rows) return launch_range(p, map, a0, 0, n_segments(p, n), stream);
+    for (int g = 0; g < p->ngroups; ++g) {
+        const auto &gr = p->groups[g];
+        fdas::OlsArgs a = a0;
+        a.H = p->d_H + (size_t)gr.first * 8 * (p->L / 16);
+        a.M = gr.count;
+        a.G = std::min(p->G, gr.count);
+        a.S = gr.S;
+        a.K = gr.K;
+        a.rows = p->d_rows + gr.first;
+        a.shifts = p->d_shifts + gr.first;
+        const int64_t span = n - gr.min_shift;
+        const int64_t nseg = span > 0 ? (span + gr.S - 1) / gr.S : 1;   // one segment writes the zero prefix
+        cudaError_t e = fdas::launch_ols_fp32(p->L, map, a, (int)nseg, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch (template group)");
+    }
+    return FDAS_OK;
+}
+
+int enqueue_segments(fdas_plan p, const CUtensorMap *map, int64_t n, float *out, int64_t s0, int64_t s1,
+                     cudaStream_t stream)
+{
+    const fdas::OlsArgs a = base_args(p, n, out);
+    if (p->precision == FDAS_PREC_TC_FP16) {
+        fdas::OlsArgs b = a;
+        b.seg_begin = (int)s0;
+        cudaError_t e = fdas::launch_ols_tc(map, b, p->d_wtc, (int)(s1 - s0), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch");
+        return FDAS_OK;
+    }
+    return launch_range(p, map, a, s0, s1, stream);
+}
+
+// Support of each template (first and last nonzero tap), the grouping that minimises the
+// number of L-point transforms for arrays of n_ref points (equal-count groups of templates
+// sorted by support length, 1 to 6 groups), and the permuted, shifted template array.
+int plan_groups(fdas_plan p, const float2 *h_host, int64_t n_ref, std::vector<float2> &shifted,
+                std::vector<int> &rows, std::vector<int> &shifts)
+{
+    const int M = p->M, K = p->K_user, L = p->L;
+    std::vector<int> first(M), len(M);
+    for (int z = 0; z < M; ++z) {
+        int a = -1, b = -1;
+        for (int k = 0; k < K; ++k) {
+            const float2 v = h_host[(size_t)z * K + k];
+            if (v.x != 0.f || v.y != 0.f) {
+                if (a < 0) a = k;
+                b = k;
+            }
+        }
+        first[z] = a < 0 ? 0 : a;
+        len[z] = a < 0 ? 1 : b - a + 1;
+    }
+    std::vector<int> order(M);
+    for (int z = 0; z < M; ++z) order[z] = z;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return len[u] < len[v]; });
+    auto frame = [](int k) { return 4 * ((k - 1 + 3) / 4) + 1; };
+    double best = 1e300;
+    int best_ng = 1;
+    for (int ng = 1; ng <= std::min(6, M); ++ng) {
+        double cost = 0;
+        for (int g = 0; g < ng; ++g) {
+            const int lo = (int)((int64_t)M * g / ng), hi = (int)((int64_t)M * (g + 1) / ng);
+            if (hi <= lo) continue;
+            const int Kg = frame(len[order[hi - 1]]), Sg = L - Kg + 1;
+            cost += (double)((n_ref + Sg - 1) / Sg) * (hi - lo + 1);
+        }
+        if (cost < best * (1.0 - 1e-9)) {
+            best = cost;
+            best_ng = ng;
+        }
+    }
+    p->ngroups = best_ng;
+    for (int g = 0; g < best_ng; ++g) {
+        const int lo = (int)((int64_t)M * g / best_ng), hi = (int)((int64_t)M * (g + 1) / best_ng);
+        auto &gr = p->groups[g];
+        gr.first = lo;
+        gr.count = hi - lo;
+        gr.K = frame(len[order[hi - 1]]);
+        gr.S = L - gr.K + 1;
+        gr.min_shift = INT64_MAX;
+        for (int r = lo; r < hi; ++r) gr.min_shift = std::min<int64_t>(gr.min_shift, first[order[r]]);
+    }
+    shifted.assign((size_t)M * K, make_float2(0.f, 0.f));
+    rows.resize(M);
+    shifts.resize(M);
+    for (int r = 0; r < M; ++r) {
+        const int z = order[r];
+        rows[r] = z;
+        shifts[r] = first[z];
+        for (int k = 0; k < len[z]; ++k) shifted[(size_t)r * K + k] = h_host[(size_t)z * K + first[z] + k];
+    }
+    return FDAS_OK;
+}
 
 // (Re)build the FP64 twiddles and the pre-transformed templates for segment length L.
 int build_templates(fdas_plan p, const float2 *d_h32, int L)
@@ -206,6 +320,7 @@ int build_templates(fdas_plan p, const float2 *d_h32, int L)
 int validate_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs)
 {
     if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");
+    if (p->d_rows) return fail(FDAS_ERR_UNSUPPORTED, "the batched forms are built for ungrouped plans");
     if (count < 0 || (count > 0 && (!ins || !ns || !outs))) return fail(FDAS_ERR_INVALID_ARG, "bad batch arrays");
     for (int i = 0; i < count; ++i) {
         int rc = validate_convolve(p, ins[i], ns[i], outs[i]);
@@ -481,6 +596,7 @@ int validate_array(fdas_plan p, const void *in, int64_t n, const float *out)
 }
 
 int plan_templates(fdas_plan p) { return p ? p->M : 0; }
+int plan_grouped(fdas_plan p) { return p && p->d_rows ? 1 : 0; }
 int64_t plan_n_max(fdas_plan p) { return p ? p->n_max : 0; }
 
 // Plan accessor and error reporting for code outside this file.
@@ -527,6 +643,9 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     if (K < 1 || K > L - 4) return fail(FDAS_ERR_INVALID_ARG, "tpl_len=%d outside [1, %d]", K, L - 4);
     if (n_max < 1 || n_max > (int64_t(1) << 30)) return fail(FDAS_ERR_INVALID_ARG, "n_max=%lld outside [1, 2^30]", (long long)n_max);
     if (o.tpl_per_cta < 0 || o.tpl_per_cta > M) return fail(FDAS_ERR_INVALID_ARG, "tpl_per_cta=%d outside [0, %d]", o.tpl_per_cta, M);
+    if (o.group_support != 0 && o.group_support != 1) return fail(FDAS_ERR_INVALID_ARG, "group_support=%d not 0 or 1", o.group_support);
+    if (o.group_support && (o.precision != FDAS_PREC_FP32 || o.autotune))
+        return fail(FDAS_ERR_UNSUPPORTED, "template groups are built for the FP32 form without autotuning");
 
     fdas_plan p = new (std::nothrow) fdas_plan_s;
     if (!p) return fail(FDAS_ERR_OOM, "host allocation");
@@ -564,12 +683,31 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
         else if ((e = fdas::launch_tc_matrices(p->d_wtc, nullptr)) != cudaSuccess) rc = cuda_fail(e, "DFT matrix kernel");
     }
     if (rc == FDAS_OK && o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
-    if (rc == FDAS_OK) rc = build_templates(p, d_h32, p->L);
     p->d_h32 = d_h32;   // kept for the time-domain form
+    if (rc == FDAS_OK && o.group_support) {
+        // transform the permuted, shifted templates instead of the raw ones
+        std::vector<float2> shifted;
+        std::vector<int> rows, shifts;
+        rc = plan_groups(p, static_cast<const float2 *>(templates), n_max, shifted, rows, shifts);
+        float2 *d_hs = nullptr;
+        if (rc == FDAS_OK && (e = cudaMalloc(&d_hs, h_bytes)) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc shifted templates");
+        if (rc == FDAS_OK && (e = cudaMalloc(&p->d_rows, sizeof(int) * M)) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc rows");
+        if (rc == FDAS_OK && (e = cudaMalloc(&p->d_shifts, sizeof(int) * M)) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc shifts");
+        if (rc == FDAS_OK && (e = cudaMemcpy(d_hs, shifted.data(), h_bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+            rc = cuda_fail(e, "copy shifted templates");
+        if (rc == FDAS_OK && (e = cudaMemcpy(p->d_rows, rows.data(), sizeof(int) * M, cudaMemcpyHostToDevice)) != cudaSuccess)
+            rc = cuda_fail(e, "copy rows");
+        if (rc == FDAS_OK && (e = cudaMemcpy(p->d_shifts, shifts.data(), sizeof(int) * M, cudaMemcpyHostToDevice)) != cudaSuccess)
+            rc = cuda_fail(e, "copy shifts");
+        if (rc == FDAS_OK) rc = build_templates(p, d_hs, p->L);
+        cudaFree(d_hs);
+    } else if (rc == FDAS_OK) {
+        rc = build_templates(p, d_h32, p->L);
+    }
     if (rc != FDAS_OK) return cleanup_fail(rc);
     p->device_bytes = (int64_t)(sizeof(float2) * p->L + sizeof(double2) * p->L +
                                 sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) + h_bytes +
-                                (p->d_wtc ? fdas::tc_matrix_bytes() : 0));
+                                (p->d_wtc ? fdas::tc_matrix_bytes() : 0) + (p->d_rows ? 2 * sizeof(int) * M : 0));
     *out = p;
     return FDAS_OK;
 }
@@ -590,6 +728,7 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *d)
     d->tuned = p->tuned;
     for (int i = 0; i < 9; ++i) d->tune_ms[i] = p->tune_ms[i / 3][i % 3];
     d->batch_blocks = p->bk.resident;
+    d->groups = p->ngroups;
     return FDAS_OK;
 }
 
@@ -613,6 +752,7 @@ int fdas_convolve(fdas_plan p, const void *in, int64_t n, float *out, void *stre
     if (!g.ok) return fail(FDAS_ERR_CUDA, "cannot select plan device %d", p->device);
     CUtensorMap map;
     if ((rc = encode_input_map(&map, in, n))) return rc;
+    if (p->d_rows) return launch_all(p, &map, base_args(p, n, out), n, (cudaStream_t)stream);
     return enqueue_segments(p, &map, n, out, 0, n_segments(p, n), (cudaStream_t)stream);
 }
 
@@ -646,24 +786,12 @@ int fdas_convolve_candidates(fdas_plan p, const void *in, int64_t n, float thres
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     FDAS_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s), "clear candidate counter");
-    fdas::OlsArgs a;
-    a.H = p->d_H;
-    a.tw = p->d_tw;
-    a.out = nullptr;
-    a.n = n;
-    a.M = p->M;
-    a.G = p->G;
-    a.S = p->S;
-    a.K = p->K;
-    a.seg_begin = 0;
-    a.status = p->d_status;
+    fdas::OlsArgs a = base_args(p, n, nullptr);
     a.cand = cand ? cand : reinterpret_cast<fdas_candidate *>(count);   // non-null selects the epilogue
     a.cand_count = count;
     a.cand_max = max_cand;
     a.threshold = threshold;
-    cudaError_t e = fdas::launch_ols_fp32(p->L, &map, a, (int)n_segments(p, n), s);
-    if (e != cudaSuccess) return cuda_fail(e, "candidate kernel launch");
-    return FDAS_OK;
+    return launch_all(p, &map, a, n, s);
 }
 
 int fdas_convolve_host(fdas_plan p, const void *in_host, int64_t n, float *out_host, void *stream)
@@ -686,6 +814,13 @@ int fdas_convolve_host(fdas_plan p, const void *in_host, int64_t n, float *out_h
     CUtensorMap map;
     int rc = encode_input_map(&map, p->d_in_stage, n);
     if (rc) return rc;
+    if (p->d_rows) {   // grouped plans: every group writes every column range, one copy at the end
+        if ((rc = launch_all(p, &map, base_args(p, n, p->d_out_stage), n, s))) return rc;
+        FDAS_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out_stage, sizeof(float) * (size_t)n * p->M, cudaMemcpyDeviceToHost, s),
+                      "D2H plane");
+        FDAS_CUDA_TRY(cudaStreamSynchronize(s), "stream sync");
+        return FDAS_OK;
+    }
     const int64_t nseg = n_segments(p, n);
     const int chunks = (int)std::min<int64_t>(kMaxChunks, nseg);
     for (int c = 0; c < chunks; ++c) {

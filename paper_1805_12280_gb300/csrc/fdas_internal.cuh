@@ -56,6 +56,10 @@ struct OlsArgs {
     unsigned long long *cand_count = nullptr;
     long long cand_max = 0;
     float threshold = 0.f;
+    // grouped plans: template z of this launch goes to plane row rows[z], its outputs shifted
+    // by shifts[z] (the first nonzero tap); outputs before the shift are zero
+    const int *rows = nullptr;
+    const int *shifts = nullptr;
 };
 
 // One array of a batch: its input tensor map (param space), output plane and work items.
@@ -102,6 +106,7 @@ int lane_launch(fdas_plan p, Lane *l, int count, const void *const *ins, const i
 void lane_free(Lane *l);
 int validate_array(fdas_plan p, const void *in, int64_t n, const float *out);
 int plan_templates(fdas_plan p);
+int plan_grouped(fdas_plan p);
 int64_t plan_n_max(fdas_plan p);
 
 // Graph-free launches of the persistent batch kernel with caller-provided work counters

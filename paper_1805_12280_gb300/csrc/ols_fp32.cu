@@ -218,6 +218,35 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     const int obase = tid - (a.K - 1);                          // output index of register slot 0
 
     for (int z = z0; z < z1; ++z) {
+        // output row and shift of this template (identity unless the plan groups templates)
+        int row = z;
+        int64_t shift = 0;
+        unsigned nv = nvalid;
+        if (a.rows) {
+            row = __ldg(&a.rows[z]);
+            shift = __ldg(&a.shifts[z]);
+            const int64_t rem = n - shift - seg_out;
+            nv = rem <= 0 ? 0u : (unsigned)(rem < a.S ? rem : a.S);
+            if (seg == 0 && shift > 0) {   // outputs before the first nonzero tap are zero
+                const int64_t lim = shift < n ? shift : n;
+                for (int64_t i = tid; i < lim; i += NT) {
+                    if constexpr (CAND) {
+                        if (0.f > a.threshold) {
+                            const unsigned long long g = atomicAdd(a.cand_count, 1ull);
+                            if (g < (unsigned long long)a.cand_max) {
+                                fdas_candidate c;
+                                c.tpl = row;
+                                c.power = 0.f;
+                                c.bin = i;
+                                a.cand[g] = c;
+                            }
+                        }
+                    } else {
+                        out[(size_t)row * (size_t)n + i] = 0.f;
+                    }
+                }
+            }
+        }
         const int buf = NHB == 2 ? ((z - z0) & 1) : 0;
         const float4 *hz = hb + buf * 8 * NT;
         const uint32_t hu = buf ? B.h_uses1 : B.h_uses0;
@@ -296,11 +325,11 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {     // static slots: pw stays in registers
                     const int o = j * NT + obase;
-                    if ((unsigned)o < nvalid && pw[j] > a.threshold) {
+                    if ((unsigned)o < nv && pw[j] > a.threshold) {
                         fdas_candidate c;
-                        c.tpl = z;
+                        c.tpl = row;
                         c.power = pw[j];
-                        c.bin = seg_out + o;
+                        c.bin = shift + seg_out + o;
                         const unsigned idx = atomicAdd(B.sc, 1u);
                         if (idx < (unsigned)kCandCap) {
                             B.sb[idx] = c;
@@ -312,11 +341,11 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
                 }
             }
         } else {
-            float *orow = out + (size_t)z * (size_t)n + seg_out;
+            float *orow = out + (size_t)row * (size_t)n + shift + seg_out;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int o = j * NT + obase;
-                if ((unsigned)o < nvalid) orow[o] = cabs2(v[j]);
+                if ((unsigned)o < nv) orow[o] = cabs2(v[j]);
             }
         }
     }

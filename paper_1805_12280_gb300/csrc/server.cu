@@ -227,6 +227,7 @@ int fdas_server_create(fdas_server *out, fdas_plan plan, const fdas_server_opts 
     if (lanes < 1 || lanes > 16) return fdas::set_error(FDAS_ERR_INVALID_ARG, "lanes outside [1, 16]");
     if (max_batch < 1 || max_batch > fdas::kBatchMax)
         return fdas::set_error(FDAS_ERR_INVALID_ARG, "max_batch outside [1, 120]");
+    if (fdas::plan_grouped(plan)) return fdas::set_error(FDAS_ERR_UNSUPPORTED, "the server is built for ungrouped plans");
     fdas_server_s *s = new (std::nothrow) fdas_server_s;
     if (!s) return fdas::set_error(FDAS_ERR_OOM, "host allocation");
     s->plan = plan;

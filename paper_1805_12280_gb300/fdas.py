@@ -36,7 +36,7 @@ class FdasError(RuntimeError):
 
 class fdas_opts(ctypes.Structure):
     _fields_ = [("seg_len", ctypes.c_int), ("tpl_per_cta", ctypes.c_int),
-                ("precision", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("autotune", ctypes.c_int), ("group_support", ctypes.c_int)]
 
 
 class fdas_plan_desc(ctypes.Structure):
@@ -44,7 +44,7 @@ class fdas_plan_desc(ctypes.Structure):
                 ("frame_len", ctypes.c_int), ("seg_len", ctypes.c_int), ("seg_step", ctypes.c_int),
                 ("tpl_per_cta", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
                 ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9),
-                ("batch_blocks", ctypes.c_int)]
+                ("batch_blocks", ctypes.c_int), ("groups", ctypes.c_int)]
 
 
 class fdas_candidate(ctypes.Structure):
@@ -251,10 +251,10 @@ class Plan:
     """
 
     def __init__(self, templates, n_max: int, seg_len: int = 2048, tpl_per_cta: int = 0,
-                 precision: int = FDAS_PREC_FP32, autotune: int = 0):
+                 precision: int = FDAS_PREC_FP32, autotune: int = 0, group_support: int = 0):
         t = np.ascontiguousarray(np.atleast_2d(templates), dtype=np.complex64)
         self.n_templates, self.tpl_len = t.shape
-        opts = fdas_opts(seg_len, tpl_per_cta, precision, autotune)
+        opts = fdas_opts(seg_len, tpl_per_cta, precision, autotune, group_support)
         self.handle = fdas_plan_create(n_max, t.ctypes.data, self.n_templates, self.tpl_len, opts)
         self.desc = fdas_plan_describe(self.handle)
 

@@ -70,6 +70,11 @@ def test_argument_errors_without_gpu(lib):
     opts = fd.fdas.fdas_opts(2048, 0, 7, 0)
     assert lib.fdas_plan_create(ctypes.byref(h), 100, ctypes.c_void_p(1), 85, 421, ctypes.byref(opts)) == \
         fd.fdas.FDAS_ERR_UNSUPPORTED
+    # template groups: FP32 form only, no autotuning, flag 0 or 1
+    for prec, tune, grp, code in ((1, 0, 1, fd.fdas.FDAS_ERR_UNSUPPORTED), (0, 1, 1, fd.fdas.FDAS_ERR_UNSUPPORTED),
+                                  (0, 0, 2, fd.fdas.FDAS_ERR_INVALID_ARG)):
+        opts = fd.fdas.fdas_opts(2048, 0, prec, tune, grp)
+        assert lib.fdas_plan_create(ctypes.byref(h), 100, ctypes.c_void_p(1), 85, 421, ctypes.byref(opts)) == code
 
 
 def test_product_package_never_imports_oracle():
