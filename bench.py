@@ -242,7 +242,7 @@ def workload_config(args, n, tpl_len):
     return {"workload": f"single SKA-sized array: N=2^{int(np.log2(n))} complex64, 85 templates (<= {tpl_len} taps), "
                         f"L={args.seg_len} overlap-save, {args.precision} segment FFTs, fp32 power plane",
             "n": n, "templates": 85, "tpl_len": tpl_len, "seg_len": args.seg_len,
-            "tpl_per_cta": args.tpl_per_cta or 85, "precision": args.precision,
+            "tpl_per_cta": args.tpl_per_cta or "per call", "precision": args.precision,
             "l2": "no flush: each step writes the 1.43 GB plane (> 129 MB L2), evicting the 33.5 MB input"}
 
 
@@ -369,6 +369,7 @@ def run_fdas(args):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": value / PAPER_ARRAYS_PER_S, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args, n, h.shape[1]),
+                "tpl_per_cta_used": fd.fdas_plan_tpl_per_cta(plan.handle, n),
                 "plane_gbs": 4.0 * m * n * world / (ms_per_step / 1e3) / 1e9,
                 "model_tflops": model_flops(n, m, args.seg_len, h.shape[1]) * world / (ms_per_step / 1e3) / 1e12,
                 "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": cpu, "e2e": e2e,
@@ -560,8 +561,8 @@ def bench_length_sweep(fd, dev, xd, lengths=(64, 128, 256, 421)):
 
 def bench_batch(fd, h, dev, reps=10):
     """Batched form: 64 dedispersion trials, N log-uniform in [2^18, 2^22], one persistent
-    launch per graph replay, (L, G) from the autotuner; beside it the same 64 arrays
-    through the per-array FP32 path (fdas_convolve, L = 2048, G = 85)."""
+    launch per graph replay, L = 2048 and G chosen per call; beside it the autotuned plan
+    and the same 64 arrays through the per-array FP32 path (fdas_convolve)."""
     import torch
     specs = synth.batch_trials()
     xs = [torch.from_numpy(synth.make_input(s)).to(dev) for s in specs]
@@ -571,15 +572,23 @@ def bench_batch(fd, h, dev, reps=10):
     res = {"workload": "64 arrays, N log-uniform in [2^18, 2^22] (seeds 1000+i), 85 templates",
            "arrays": len(xs), "total_points": total_n,
            "plane_bytes": 4 * h.shape[0] * total_n}
+    with fd.Plan(h, n_max=1 << 22) as plan:
+        for _ in range(3):
+            plan.convolve_batch(xs, outs, stream)
+        ms = _events_ms(lambda: plan.convolve_batch(xs, outs, stream), reps, stream)
+        plan.status(stream)
+        res.update({"seg_len": plan.desc.seg_len, "tpl_per_cta": "per call",
+                    "ms_per_batch": ms, "arrays_per_s": len(xs) / (ms / 1e3),
+                    "plane_gbs": res["plane_bytes"] / (ms / 1e3) / 1e9, "gpu_launches_per_batch": 1})
     with fd.Plan(h, n_max=1 << 22, autotune=1) as plan:
         d = plan.desc
         for _ in range(3):
             plan.convolve_batch(xs, outs, stream)
         ms = _events_ms(lambda: plan.convolve_batch(xs, outs, stream), reps, stream)
         plan.status(stream)
-        res.update({"seg_len": d.seg_len, "tpl_per_cta": d.tpl_per_cta, "tune_ms": [round(v, 4) for v in d.tune_ms],
-                    "ms_per_batch": ms, "arrays_per_s": len(xs) / (ms / 1e3),
-                    "plane_gbs": res["plane_bytes"] / (ms / 1e3) / 1e9, "gpu_launches_per_batch": 1})
+        res["autotuned"] = {"seg_len": d.seg_len, "tpl_per_cta": d.tpl_per_cta,
+                            "tune_ms": [round(v, 4) for v in d.tune_ms], "ms_per_batch": ms,
+                            "arrays_per_s": len(xs) / (ms / 1e3)}
     with fd.Plan(h, n_max=1 << 22) as plan:
         def per_array():
             for x, o in zip(xs, outs):
@@ -605,7 +614,7 @@ def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=3
     res = {"workload": f"Poisson {rate:g} arrays/s for {duration:g} s ({count} requests), N log-uniform in "
                        f"[2^16, 2^22] (arrival seed 2000, {pool_size} distinct arrays 2001+i), budget "
                        f"{budget / 1e9:g} GB", "requests": count}
-    with fd.Plan(h, n_max=1 << 22, tpl_per_cta=17) as plan:
+    with fd.Plan(h, n_max=1 << 22) as plan:
         stream = torch.cuda.current_stream(dev)
         outs = [torch.empty((h.shape[0], x.numel()), dtype=torch.float32, device=dev) for x in pool]
 

@@ -49,7 +49,9 @@ typedef struct fdas_plan_s *fdas_plan;
 /* Plan options; a zero-initialised struct (or NULL) selects the defaults. */
 typedef struct {
     int seg_len;      /* L, the overlap-save FFT length: 1024, 2048 or 4096 (0 = 2048) */
-    int tpl_per_cta;  /* G, templates per thread block: 1..M (0 = all M) */
+    int tpl_per_cta;  /* G, templates per thread block: 1..M; 0 = chosen per call from the number
+                         of segments (all M for long arrays, fewer per block for short ones so
+                         that the launch still fills the GPU; the tensor-core form uses all M) */
     int precision;    /* FDAS_PREC_* (0 = FP32) */
     int autotune;     /* 1: time every (L in {1024, 2048, 4096}) x (G in {5, 17, 85}) with the
                          persistent kernel on one array of min(n_max, 2^21) points and keep the
@@ -72,7 +74,7 @@ typedef struct {
                              frame_len - 1 is a multiple of 4 (the convolution is unchanged) */
     int     seg_len;      /* L */
     int     seg_step;     /* S: valid outputs per segment, a multiple of 4, <= L - frame_len + 1 */
-    int     tpl_per_cta;  /* G */
+    int     tpl_per_cta;  /* G (0: chosen per call) */
     int     precision;    /* FDAS_PREC_* */
     int     device;       /* CUDA device ordinal the plan lives on */
     int64_t device_bytes; /* device memory owned by the plan */
@@ -102,6 +104,12 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates_c64_ho
 
 /* Fill *desc with the plan's parameters.  Errors: INVALID_ARG. */
 int fdas_plan_describe(fdas_plan p, fdas_plan_desc *desc);
+
+/* Templates per thread block that fdas_convolve uses for an array of n points (the plan's
+ * fixed G, or the per-call choice when the plan was created with tpl_per_cta = 0).
+ * Returns G >= 1, or a negative error code (INVALID_ARG for a null plan or n outside
+ * [1, n_max]).  Host only; no CUDA call. */
+int fdas_plan_tpl_per_cta(fdas_plan p, int64_t n);
 
 /*
  * fdas_convolve -- power plane of one array (the hot path).

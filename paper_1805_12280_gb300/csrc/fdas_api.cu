@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -98,6 +99,7 @@ struct fdas_plan_s {
     int device = -1;
     int64_t n_max = 0;
     int M = 0, K_user = 0, K = 0, L = 0, S = 0, G = 0, precision = 0;
+    int g_auto = 0;             // 1: templates per block chosen per call from the segment count
     float2 *d_tw = nullptr;     // [L] FP32 twiddles
     double2 *d_tw64 = nullptr;  // [L] FP64 twiddles
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
@@ -168,6 +170,22 @@ int validate_convolve(fdas_plan p, const void *in, int64_t n, const float *out)
 
 int64_t n_segments(const fdas_plan p, int64_t n) { return (n + p->S - 1) / p->S; }
 
+// Templates per block for a launch over `nseg` segments of `m` templates.  A plan with a
+// fixed G keeps it.  Otherwise the templates are split into ng groups so that short arrays
+// still fill the GPU: ng = (4 * resident blocks / nseg)^0.7, rounded, between 1 and m/5.
+// One group per block costs a forward FFT and the segment load; the exponent and the
+// limit of five templates per block were fitted to measured times for 2^14..2^22 points
+// and 85 templates (a full-size array keeps all templates in one block).
+int call_G(const fdas_plan p, int64_t nseg, int m)
+{
+    if (!p->g_auto) return std::min(p->G, m);
+    const int slots = std::max(1, p->bk.resident);
+    const double r = 4.0 * slots / (double)std::max<int64_t>(1, nseg);
+    int ng = (int)std::lround(std::pow(r, 0.7));
+    ng = std::max(1, std::min(ng, std::max(1, m / 5)));
+    return (m + ng - 1) / ng;
+}
+
 fdas::OlsArgs base_args(fdas_plan p, int64_t n, float *out)
 {
     fdas::OlsArgs a;
@@ -176,7 +194,7 @@ fdas::OlsArgs base_args(fdas_plan p, int64_t n, float *out)
     a.out = out;
     a.n = n;
     a.M = p->M;
-    a.G = p->G;
+    a.G = call_G(p, n_segments(p, n), p->M);
     a.S = p->S;
     a.K = p->K;
     a.seg_begin = 0;
@@ -202,13 +220,13 @@ int launch_all(fdas_plan p, const CUtensorMap *map, const fdas::OlsArgs &a0, int
         fdas::OlsArgs a = a0;
         a.H = p->d_H + (size_t)gr.first * 8 * (p->L / 16);
         a.M = gr.count;
-        a.G = std::min(p->G, gr.count);
         a.S = gr.S;
         a.K = gr.K;
         a.rows = p->d_rows + gr.first;
         a.shifts = p->d_shifts + gr.first;
         const int64_t span = n - gr.min_shift;
         const int64_t nseg = span > 0 ? (span + gr.S - 1) / gr.S : 1;   // one segment writes the zero prefix
+        a.G = call_G(p, nseg, gr.count);
         cudaError_t e = fdas::launch_ols_fp32(p->L, map, a, (int)nseg, stream);
         if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch (template group)");
     }
@@ -457,13 +475,15 @@ int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *
     a.H = p->d_H;
     a.tw = p->d_tw;
     a.M = p->M;
-    a.G = p->G;
     a.S = p->S;
     a.K = p->K;
     a.status = p->d_status;
-    const int ngroups = (p->M + p->G - 1) / p->G;
     for (int c = 0; c < chunks; ++c) {
         const int first = c * kBatchMax, cnt = std::min(kBatchMax, count - first);
+        int64_t segs = 0;
+        for (int i = 0; i < cnt; ++i) segs += n_segments(p, ns[first + i]);
+        a.G = call_G(p, segs, p->M);
+        const int ngroups = (p->M + a.G - 1) / a.G;
         int64_t items = 0;
         for (int i = 0; i < cnt; ++i) {
             BatchArray &ar = t.arr[i];
@@ -541,7 +561,10 @@ static int lane_chunk(fdas_plan p, Lane *l, int first, int cnt, const void *cons
                       float *const *outs, cudaStream_t stream)
 {
     BatchTable &t = *l->table;
-    const int ngroups = (p->M + p->G - 1) / p->G;
+    int64_t segs = 0;
+    for (int i = 0; i < cnt; ++i) segs += n_segments(p, ns[first + i]);
+    const int G = call_G(p, segs, p->M);
+    const int ngroups = (p->M + G - 1) / G;
     int64_t items = 0;
     for (int i = 0; i < cnt; ++i) {
         BatchArray &a = t.arr[i];
@@ -560,7 +583,7 @@ static int lane_chunk(fdas_plan p, Lane *l, int first, int cnt, const void *cons
     a.H = p->d_H;
     a.tw = p->d_tw;
     a.M = p->M;
-    a.G = p->G;
+    a.G = G;
     a.S = p->S;
     a.K = p->K;
     a.status = p->d_status;
@@ -662,6 +685,7 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     p->S = (L - p->K + 1) & ~3;                 // multiple of 4, <= L - K + 1
     p->G = o.tpl_per_cta ? o.tpl_per_cta : M;
     p->precision = o.precision;
+    p->g_auto = (o.tpl_per_cta == 0 && !o.autotune && o.precision == FDAS_PREC_FP32) ? 1 : 0;
 
     auto cleanup_fail = [&](int code) {
         plan_free(p);
@@ -721,7 +745,7 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *d)
     d->frame_len = p->K;
     d->seg_len = p->L;
     d->seg_step = p->S;
-    d->tpl_per_cta = p->G;
+    d->tpl_per_cta = p->g_auto ? 0 : p->G;
     d->precision = p->precision;
     d->device = p->device;
     d->device_bytes = p->device_bytes;
@@ -730,6 +754,13 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *d)
     d->batch_blocks = p->bk.resident;
     d->groups = p->ngroups;
     return FDAS_OK;
+}
+
+int fdas_plan_tpl_per_cta(fdas_plan p, int64_t n)
+{
+    if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");
+    if (n < 1 || n > p->n_max) return fail(FDAS_ERR_INVALID_ARG, "n=%lld outside [1, n_max=%lld]", (long long)n, (long long)p->n_max);
+    return call_G(p, n_segments(p, n), p->M);
 }
 
 int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns, float *const *outs,

@@ -5,13 +5,19 @@
 
 namespace fdas {
 
-// Forward L-point FFT of the segment in e1 (natural order) by the NT = L/16 threads of a
-// block: passes A and B exchange through e2 and e1, pass C leaves the spectrum in X
-// ("C distribution": slot g*R + k3 of thread t holds X[k1 + 16 k2 + 16 Q k3] with
-// k1 = t % 16, k2 = t / 16 + (NT/16) g).  Ends before the barrier that must follow it.
-template <int L>
-__device__ __forceinline__ void forward_fft(float2 *e1, float2 *e2, const float2 *__restrict__ tw, float2 (&v)[16],
-                                            float2 (&X)[16])
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// Forward L-point FFT of the segment in `src` (natural order; e1 or another buffer) by the
+// NT = L/16 threads of a block: passes A and B exchange through e2 and e1, pass C leaves the
+// spectrum in X ("C distribution": slot g*R + k3 of thread t holds X[k1 + 16 k2 + 16 Q k3]
+// with k1 = t % 16, k2 = t / 16 + (NT/16) g).  `after_a` runs in every thread after the
+// barrier that follows pass A, when no thread reads `src` any more.  Ends before the barrier
+// that must follow it.
+template <int L, class Hook = NoHook>
+__device__ __forceinline__ void forward_fft(const float2 *src, float2 *e1, float2 *e2, const float2 *__restrict__ tw,
+                                            float2 (&v)[16], float2 (&X)[16], Hook after_a = Hook())
 {
     using Gm = Geo<L>;
     constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
@@ -19,13 +25,14 @@ __device__ __forceinline__ void forward_fft(float2 *e1, float2 *e2, const float2
     const int tid = threadIdx.x, k1 = tid & 15, hi = tid >> 4;
     // ---- forward pass A: 16-point DFT over the top digit, twiddle W_L^{t k1}
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = e1[j * NT + tid];
+    for (int j = 0; j < 16; ++j) v[j] = src[j * NT + tid];
     dft<16, -1>(v);
 #pragma unroll
     for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(&tw[(tid * k) & MASK]));
 #pragma unroll
     for (int k = 0; k < 16; ++k) e2[tid + LD2 * k] = v[k];
     __syncthreads();
+    after_a();
     // ---- forward pass B: Q-point DFT over b, twiddle W_{QR}^{c k2}
 #pragma unroll
     for (int g = 0; g < GB; ++g) {
@@ -54,6 +61,14 @@ __device__ __forceinline__ void forward_fft(float2 *e1, float2 *e2, const float2
     }
     dft<R, -1, 1, 0>(X);
     if constexpr (GC == 2) dft<R, -1, 1, R>(X);
+}
+
+// The segment in e1.
+template <int L>
+__device__ __forceinline__ void forward_fft(float2 *e1, float2 *e2, const float2 *__restrict__ tw, float2 (&v)[16],
+                                            float2 (&X)[16])
+{
+    forward_fft<L>(e1, e1, e2, tw, v, X);
 }
 
 }  // namespace fdas

@@ -162,12 +162,23 @@ __device__ __noinline__ void drain(uint64_t *bar, unsigned pending, unsigned par
         if (pending & (1u << i)) mbar_wait_bounded(&bar[i], (parity >> i) & 1u, kWaitLimitNs);
 }
 
+// No item follows (one item per block).
+struct NoNext {
+    __device__ __forceinline__ bool operator()(const CUtensorMap **, int *) const { return false; }
+};
+
 // One work item.  Every thread of the block calls it with the same arguments after a
 // block-wide barrier that follows the previous item.  Returns false (block-uniformly)
 // if a bounded wait ran out; the status bit is then set.
-template <int L, bool CAND = false>
+//
+// Cross-item prefetch (single template buffer only): when thread 0's `next` names the
+// following item's input (tensor map and first coordinate), its segment is loaded into the
+// template buffer as soon as the last template of this item has been read; the following
+// item is then called with `prefetched` set, transforms the segment from there and loads
+// its first template only after the forward pass A.
+template <int L, bool CAND = false, class Next = NoNext>
 __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CUtensorMap *map, int seg, int z0,
-                                         int z1, int64_t n, float *out)
+                                         int z1, int64_t n, float *out, bool prefetched = false, Next next = Next())
 {
     using Gm = Geo<L>;
     constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
@@ -179,7 +190,9 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     uint64_t *bar = B.bar;
     const int tid = threadIdx.x, k1 = tid & 15, hi = tid >> 4;
 
-    if (tid == 0) {
+    static_assert(NHB == 2 || HBYTES == L * sizeof(float2), "a prefetched segment fills the template buffer");
+    static_assert(NHB == 2 || (sizeof(float2) * (L + 16 * Gm::LD2)) % 128 == 0, "TMA destination alignment");
+    if (tid == 0 && !prefetched) {
         fence_proxy_async_smem();   // earlier generic writes to e1/hb are ordered before the async copies
         mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)));
         const int c0 = seg * a.S - (a.K - 1);
@@ -196,7 +209,7 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     if (!__syncthreads_and(seg_ok)) {
         if (tid == 0) {
             atomicOr(a.status, STATUS_WAIT_TIMEOUT);
-            const unsigned pending = 1u | 2u | (NHB == 2 && z0 + 1 < z1 ? 4u : 0u);
+            const unsigned pending = prefetched ? 1u : (1u | 2u | (NHB == 2 && z0 + 1 < z1 ? 4u : 0u));
             const unsigned parity = ((B.seg_uses - 1) & 1u) | ((B.h_uses0 & 1u) << 1) | ((B.h_uses1 & 1u) << 2);
             drain(bar, pending, parity);
         }
@@ -207,7 +220,16 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     const uint32_t my = tmem_lane_addr(B.tmem, (uint32_t)(tid >> 7) * kColGroup);
     {
         float2 X[16];
-        forward_fft<L>(e1, e2, a.tw, v, X);
+        if (prefetched) {   // segment in the template buffer: its first template follows pass A
+            forward_fft<L>(reinterpret_cast<const float2 *>(hb), e1, e2, a.tw, v, X, [&]() {
+                if (tid == 0) {
+                    mbar_arrive_expect_tx(&bar[1], HBYTES);
+                    bulk_load(hb, a.H + (size_t)z0 * 8 * NT, HBYTES, &bar[1]);
+                }
+            });
+        } else {
+            forward_fft<L>(e1, e2, a.tw, v, X);
+        }
         tmem_st_c16(my + kColX, X);   // the spectrum waits in TMEM for the template loop
     }
     __syncthreads();   // every thread has read e1 before the template loop rewrites it
@@ -283,10 +305,22 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
             }
             return false;
         }
-        // every thread has read hb[buf]: refill it with the template NHB ahead
-        if (tid == 0 && z + NHB < z1) {
-            mbar_arrive_expect_tx(&bar[1 + buf], HBYTES);
-            bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + NHB) * 8 * NT, HBYTES, &bar[1 + buf]);
+        // every thread has read hb[buf]: refill it with the template NHB ahead, or, after the
+        // last template, with the following item's segment
+        if (tid == 0) {
+            if (z + NHB < z1) {
+                mbar_arrive_expect_tx(&bar[1 + buf], HBYTES);
+                bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + NHB) * 8 * NT, HBYTES, &bar[1 + buf]);
+            } else if (NHB == 1 && z + 1 == z1) {
+                const CUtensorMap *nmap;
+                int nc0;
+                if (next(&nmap, &nc0)) {
+                    mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)));
+                    float2 *dst = reinterpret_cast<float2 *>(hb);
+#pragma unroll
+                    for (int j = 0; j < L / 256; ++j) tma_load_1d(dst + 256 * j, nmap, nc0 + 256 * j, &bar[0]);
+                }
+            }
         }
         // ---- inverse pass B': Q-point IDFT over k2, twiddle conj W_L^{(bR + c) k1}
 #pragma unroll
@@ -382,9 +416,22 @@ __global__ void __launch_bounds__(L / 16, MINB)
     release_block<L>(B);
 }
 
+// Array of a batch item: the last array whose first item is <= item.
+__device__ __forceinline__ int batch_array_of(const BatchTable &tab, int64_t item)
+{
+    int lo = 0, hi = tab.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab.arr[mid].item_off <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Persistent: resident blocks take items (array, group, segment) from *counter until the
 // table is exhausted.  Items are numbered array by array, group-major inside an array, so
-// concurrently running blocks share templates and neighbouring segments in L2.
+// concurrently running blocks share templates and neighbouring segments in L2.  Thread 0
+// takes the following item's number while the current one runs and, with a single template
+// buffer, prefetches that item's segment behind the current item's last template.
 template <int L, int MINB>
 __global__ void __launch_bounds__(L / 16, MINB)
     ols_fp32_batch(const __grid_constant__ BatchTable tab, const OlsArgs a, int *counter)
@@ -393,22 +440,30 @@ __global__ void __launch_bounds__(L / 16, MINB)
     __shared__ int item_sh;
     Block<L> B(smem_raw);
     init_block<L>(B, a);
-    for (;;) {
-        __syncthreads();                       // the previous item is finished by every thread
-        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
-        __syncthreads();
-        const int64_t item = item_sh;
-        if (item >= tab.total_items) break;
-        int lo = 0, hi = tab.count - 1;        // last array whose first item <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab.arr[mid].item_off <= item) lo = mid; else hi = mid - 1;
-        }
-        const BatchArray &ar = tab.arr[lo];
+    if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
+    __syncthreads();
+    int64_t item = item_sh;
+    bool prefetched = false;
+    while (item < tab.total_items) {
+        const BatchArray &ar = tab.arr[batch_array_of(tab, item)];
         const int64_t local = item - ar.item_off;
         const int g = (int)(local / ar.nseg), seg = (int)(local % ar.nseg);
         const int z0 = g * a.G;
-        if (!run_item<L>(B, a, &ar.map, seg, z0, min(z0 + a.G, a.M), ar.n, ar.out)) break;
+        int64_t nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(counter, 1);   // consumed at the last template
+        auto next = [&](const CUtensorMap **m, int *c0) -> bool {
+            if (nxt >= tab.total_items) return false;
+            const BatchArray &na = tab.arr[batch_array_of(tab, nxt)];
+            *m = &na.map;
+            *c0 = (int)((nxt - na.item_off) % na.nseg) * a.S - (a.K - 1);
+            return true;
+        };
+        if (!run_item<L>(B, a, &ar.map, seg, z0, min(z0 + a.G, a.M), ar.n, ar.out, prefetched, next)) break;
+        __syncthreads();                       // every thread has read item_sh
+        if (threadIdx.x == 0) item_sh = (int)nxt;
+        __syncthreads();
+        item = item_sh;
+        prefetched = hbuf<L>() == 1 && item < tab.total_items;
     }
     release_block<L>(B);
 }

@@ -77,6 +77,7 @@ _I64 = ctypes.c_int64
 SIGNATURES = {
     "fdas_plan_create": (_I, [ctypes.POINTER(_P), _I64, _P, _I, _I, ctypes.POINTER(fdas_opts)]),
     "fdas_plan_describe": (_I, [_P, ctypes.POINTER(fdas_plan_desc)]),
+    "fdas_plan_tpl_per_cta": (_I, [_P, _I64]),
     "fdas_convolve": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_host": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_batch": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
@@ -144,6 +145,12 @@ def fdas_plan_describe(plan: int) -> fdas_plan_desc:
     d = fdas_plan_desc()
     _check(load().fdas_plan_describe(_P(plan), ctypes.byref(d)), "fdas_plan_describe")
     return d
+
+
+def fdas_plan_tpl_per_cta(plan: int, n: int) -> int:
+    g = load().fdas_plan_tpl_per_cta(_P(plan), int(n))
+    _check(min(g, 0), "fdas_plan_tpl_per_cta")
+    return g
 
 
 def fdas_convolve(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:

@@ -57,6 +57,7 @@ def test_argument_errors_without_gpu(lib):
     # null handles and out-of-range sizes are rejected before any CUDA call
     assert lib.fdas_convolve(None, None, 10, None, None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_destroy(None) == fd.fdas.FDAS_ERR_INVALID_ARG
+    assert lib.fdas_plan_tpl_per_cta(None, 10) == fd.fdas.FDAS_ERR_INVALID_ARG
     h = ctypes.c_void_p()
     opts = fd.fdas.fdas_opts(3000, 0, 0, 0)
     assert lib.fdas_plan_create(ctypes.byref(h), 100, ctypes.c_void_p(1), 85, 421, ctypes.byref(opts)) == \

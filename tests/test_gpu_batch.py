@@ -44,6 +44,28 @@ def test_batch_equals_single_array_path(fd, oracle_mod, bank, L, G):
         compare(outs[i].cpu().numpy(), oracle_mod.ols_power(x, bank), TOL_FP32)
 
 
+def test_templates_per_block_chosen_per_call(fd, oracle_mod, bank):
+    # tpl_per_cta = 0: all 85 templates per block for a full-size array, fewer for short
+    # arrays (more blocks); the bits do not depend on the choice
+    with fd.Plan(bank, n_max=1 << 22) as plan:
+        assert plan.desc.tpl_per_cta == 0
+        gs = [fd.fdas_plan_tpl_per_cta(plan.handle, 1 << k) for k in range(10, 23)]
+        assert gs[-1] == 85 and gs[0] == 5
+        assert all(a <= b for a, b in zip(gs, gs[1:]))           # non-decreasing in n
+        ns = [1, 3000, 1 << 16, 300000]
+        xs = [torch.from_numpy(_rand(n, 800 + n)).cuda() for n in ns]
+        outs = plan.convolve_batch(xs)
+        singles = [plan.convolve(x) for x in xs]
+        plan.status()
+    with fd.Plan(bank, n_max=1 << 22, tpl_per_cta=85) as fixed:
+        assert fd.fdas_plan_tpl_per_cta(fixed.handle, 1 << 10) == 85
+        ref = [fixed.convolve(x) for x in xs]
+        fixed.status()
+    for o, s, r in zip(outs, singles, ref):
+        assert torch.equal(o, s) and torch.equal(s, r)
+    compare(singles[2].cpu().numpy(), oracle_mod.ols_power(xs[2].cpu().numpy(), bank), TOL_FP32)
+
+
 def test_batch_more_than_one_table(fd, oracle_mod, bank):
     # more arrays than fit one kernel-parameter table (120): several graph replays
     ns = [(37 * i) % 3001 + 1 for i in range(130)]
