@@ -45,19 +45,40 @@ __device__ __forceinline__ void forward_fft(const float2 *src, float2 *e1, float
 #pragma unroll
     for (int g = 0; g < GB; ++g) {
         const int cg = hi + (NT / 16) * g;
+        if constexpr (GC == 2) {
+            // k2 and k2 + Q/2 share one 16-byte slot, k1 + 16 (k2 mod Q/2) + 8 Q c: pass C
+            // holds both and reads them with one load
+            static_assert(NT / 16 == Q / 2, "paired exchange layout");
+            float4 *e1q = reinterpret_cast<float4 *>(e1);
 #pragma unroll
-        for (int k2 = 0; k2 < Q; ++k2) {
-            const float2 w = (k2 == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[(16 * cg * k2) & MASK]);
-            e1[k1 + 16 * k2 + 16 * Q * cg] = cmul(v[g * Q + k2], w);
+            for (int k2 = 0; k2 < Q / 2; ++k2) {
+                const float2 w0 = (k2 == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[(16 * cg * k2) & MASK]);
+                const float2 w1 = __ldg(&tw[(16 * cg * (k2 + Q / 2)) & MASK]);
+                const float2 u0 = (k2 == 0) ? v[g * Q] : cmul(v[g * Q + k2], w0);
+                const float2 u1 = cmul(v[g * Q + k2 + Q / 2], w1);
+                e1q[k1 + 16 * k2 + 8 * Q * cg] = make_float4(u0.x, u0.y, u1.x, u1.y);
+            }
+        } else {
+#pragma unroll
+            for (int k2 = 0; k2 < Q; ++k2) {
+                const float2 w = (k2 == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[(16 * cg * k2) & MASK]);
+                e1[k1 + 16 * k2 + 16 * Q * cg] = cmul(v[g * Q + k2], w);
+            }
         }
     }
     __syncthreads();
     // ---- forward pass C: R-point DFT over c; spectrum stays in registers
+    if constexpr (GC == 2) {
+        const float4 *e1q = reinterpret_cast<const float4 *>(e1);
 #pragma unroll
-    for (int g = 0; g < GC; ++g) {
-        const int k2 = hi + (NT / 16) * g;
+        for (int c = 0; c < R; ++c) {
+            const float4 w = e1q[k1 + 16 * hi + 8 * Q * c];
+            X[c] = make_float2(w.x, w.y);
+            X[R + c] = make_float2(w.z, w.w);
+        }
+    } else {
 #pragma unroll
-        for (int c = 0; c < R; ++c) X[g * R + c] = e1[k1 + 16 * k2 + 16 * Q * c];
+        for (int c = 0; c < R; ++c) X[c] = e1[k1 + 16 * hi + 16 * Q * c];
     }
     dft<R, -1, 1, 0>(X);
     if constexpr (GC == 2) dft<R, -1, 1, R>(X);

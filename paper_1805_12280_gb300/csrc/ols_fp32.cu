@@ -182,7 +182,6 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
 {
     using Gm = Geo<L>;
     constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
-    constexpr int MASK = L - 1;
     constexpr uint32_t HBYTES = (uint32_t)Smem<L>::h_bytes;
     constexpr int NHB = hbuf<L>();
     float2 *e1 = B.e1, *e2 = B.e2;
@@ -287,12 +286,21 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
         if constexpr (GC == 2) dft<R, 1, 1, R>(v);
         float2 tw1[16];
         tmem_ld_c16(my + kColTw1, tw1);
+        if constexpr (GC == 2) {
+            // the thread's two k2 values (hi and hi + Q/2) of each c share one 16-byte slot:
+            // k1 + 16 (k2 mod Q/2) + 8 Q c; pass B' reads both halves with one load
+            static_assert(NT / 16 == Q / 2, "paired exchange layout");
+            float4 *e1q = reinterpret_cast<float4 *>(e1);
 #pragma unroll
-        for (int g = 0; g < GC; ++g) {
-            const int k2 = hi + (NT / 16) * g;
+            for (int c = 0; c < R; ++c) {
+                const float2 u0 = (c == 0) ? v[0] : cmul(v[c], tw1[c]);
+                const float2 u1 = (c == 0) ? v[R] : cmul(v[R + c], tw1[R + c]);
+                e1q[k1 + 16 * hi + 8 * Q * c] = make_float4(u0.x, u0.y, u1.x, u1.y);
+            }
+        } else {
 #pragma unroll
             for (int c = 0; c < R; ++c)
-                e1[k1 + 16 * k2 + 16 * Q * c] = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
+                e1[k1 + 16 * hi + 16 * Q * c] = (c == 0) ? v[0] : cmul(v[c], tw1[c]);
         }
         if (!__syncthreads_and(h_ok)) {      // a template buffer never arrived: leave together
             if (tid == 0) {
@@ -326,8 +334,18 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
             const int cg = hi + (NT / 16) * g;
+            if constexpr (GC == 2) {
+                const float4 *e1q = reinterpret_cast<const float4 *>(e1);
 #pragma unroll
-            for (int k2 = 0; k2 < Q; ++k2) v[g * Q + k2] = e1[k1 + 16 * k2 + 16 * Q * cg];
+                for (int k2 = 0; k2 < Q / 2; ++k2) {
+                    const float4 w = e1q[k1 + 16 * k2 + 8 * Q * cg];
+                    v[g * Q + k2] = make_float2(w.x, w.y);
+                    v[g * Q + k2 + Q / 2] = make_float2(w.z, w.w);
+                }
+            } else {
+#pragma unroll
+                for (int k2 = 0; k2 < Q; ++k2) v[g * Q + k2] = e1[k1 + 16 * k2 + 16 * Q * cg];
+            }
         }
         dft<Q, 1, 1, 0>(v);
         if constexpr (GB == 2) dft<Q, 1, 1, Q>(v);
