@@ -176,7 +176,12 @@ struct NoNext {
 // template buffer as soon as the last template of this item has been read; the following
 // item is then called with `prefetched` set, transforms the segment from there and loads
 // its first template only after the forward pass A.
-template <int L, bool CAND = false, class Next = NoNext>
+//
+// VMASK: the plane stores test a bit mask of the thread's kept slots (per item; per template
+// near the array end for grouped plans) instead of comparing each output index: fewer instructions per
+// template in the one-item kernel; the persistent kernel, at its register limit, runs faster
+// without it.
+template <int L, bool CAND = false, class Next = NoNext, bool VMASK = false>
 __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CUtensorMap *map, int seg, int z0,
                                          int z1, int64_t n, float *out, bool prefetched = false, Next next = Next())
 {
@@ -237,17 +242,28 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
     const int64_t nvalid64 = n - seg_out;
     const unsigned nvalid = (unsigned)(nvalid64 < a.S ? nvalid64 : a.S);
     const int obase = tid - (a.K - 1);                          // output index of register slot 0
+    unsigned vmask0 = 0;   // bit j: register slot j of this thread holds a kept output
+    if constexpr (VMASK) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) vmask0 |= ((unsigned)(j * NT + obase) < nvalid ? 1u : 0u) << j;
+    }
 
     for (int z = z0; z < z1; ++z) {
         // output row and shift of this template (identity unless the plan groups templates)
         int row = z;
         int64_t shift = 0;
         unsigned nv = nvalid;
+        unsigned vmask = vmask0;
         if (a.rows) {
             row = __ldg(&a.rows[z]);
             shift = __ldg(&a.shifts[z]);
             const int64_t rem = n - shift - seg_out;
             nv = rem <= 0 ? 0u : (unsigned)(rem < a.S ? rem : a.S);
+            if (VMASK && nv != nvalid) {   // only near the end of the array
+                vmask = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) vmask |= ((unsigned)(j * NT + obase) < nv ? 1u : 0u) << j;
+            }
             if (seg == 0 && shift > 0) {   // outputs before the first nonzero tap are zero
                 const int64_t lim = shift < n ? shift : n;
                 for (int64_t i = tid; i < lim; i += NT) {
@@ -394,10 +410,16 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
             }
         } else {
             float *orow = out + (size_t)row * (size_t)n + shift + seg_out;
+            if constexpr (VMASK) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int o = j * NT + obase;
-                if ((unsigned)o < nv) orow[o] = cabs2(v[j]);
+                for (int j = 0; j < 16; ++j)
+                    if (vmask & (1u << j)) orow[j * NT + obase] = cabs2(v[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int o = j * NT + obase;
+                    if ((unsigned)o < nv) orow[o] = cabs2(v[j]);
+                }
             }
         }
     }
@@ -430,7 +452,7 @@ __global__ void __launch_bounds__(L / 16, MINB)
     }
     init_block<L>(B, a);   // its barriers also publish *B.sc = 0
     const int z0 = blockIdx.y * a.G;
-    run_item<L, CAND>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out);
+    run_item<L, CAND, NoNext, !CAND>(B, a, &tmap, a.seg_begin + blockIdx.x, z0, min(z0 + a.G, a.M), a.n, a.out);
     release_block<L>(B);
 }
 
