@@ -63,7 +63,7 @@ template <int L>
 constexpr uint32_t kTmemCols = (L / 16 > 128) ? 256u : 128u;
 constexpr uint32_t kColTw1 = 0, kColTw2 = 32, kColX = 64, kColGroup = 96;
 
-constexpr int kCandCap = 1024;   // candidates staged per block before one global reservation
+constexpr int kCandCap = 256;    // candidates staged per block before one global reservation (4 KB: four blocks per SM still fit)
 constexpr size_t kCandSmem = sizeof(fdas_candidate) * kCandCap + 16;
 
 template <int L>

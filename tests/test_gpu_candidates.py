@@ -92,7 +92,7 @@ def test_candidates_reject_tensor_core_plan(fd, bank):
 
 @pytest.mark.parametrize("threshold", [0.5, -1.0])
 def test_candidates_past_the_block_staging(fd, bank, threshold):
-    # low thresholds put more than the 1024 staged slots of a block into the list: the rest
+    # low thresholds put more than the staged slots of a block into the list: the rest
     # goes straight to global memory; T < 0 selects every output of the plane
     n = 20000
     x = synth.make_input(synth.single_small(n=n, seed=33))

@@ -32,10 +32,11 @@ def _rand(n, seed):
     return torch.from_numpy((rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)).cuda()
 
 
-def test_result_same_alone_and_in_the_mix(fd, oracle_mod, bank):
+@pytest.mark.parametrize("G", [17, 0])     # 0: templates per block chosen per batch
+def test_result_same_alone_and_in_the_mix(fd, oracle_mod, bank, G):
     x_np = synth.make_input(synth.single_small(n=40000, seed=21))
     x = torch.from_numpy(x_np).cuda()
-    with fd.Plan(bank, n_max=1 << 18, tpl_per_cta=17) as plan:
+    with fd.Plan(bank, n_max=1 << 18, tpl_per_cta=G) as plan:
         single = plan.convolve(x).clone()
         with fd.Server(plan, budget_bytes=2 << 30, lanes=3, max_batch=8) as srv:
             t = srv.submit(x)

@@ -34,11 +34,12 @@ def _inputs(ns, seed):
             for n in ns]
 
 
-def test_noalloc_batch_matches_batch_twice(fd):
+@pytest.mark.parametrize("G", [17, 0])     # 0: templates per block chosen per launch
+def test_noalloc_batch_matches_batch_twice(fd, G):
     import synth
     bank = synth.template_bank()[0]
     ns = [1, 1629, 7000, 33333, 4096, 12]
-    with fd.Plan(bank, n_max=max(ns), tpl_per_cta=17) as plan:
+    with fd.Plan(bank, n_max=max(ns), tpl_per_cta=G) as plan:
         for call in range(2):                           # two calls in a row share the counters
             xs = _inputs(ns, seed=40 + call)
             ref = plan.convolve_batch(xs)               # the existing entry point
