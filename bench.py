@@ -356,6 +356,7 @@ def run_fdas(args):
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
                  "template_groups": bench_groups(fd, h, dev, xd),
                  "library_unfused_ols": bench_library_ols(h, dev, xd),
+                 "full_fdfir": bench_fdfir(fd, h, dev, xd),
                  "library_full_fdfir": bench_library_fdfir(h, dev, xd),
                  "length_sweep": bench_length_sweep(fd, dev, xd),
                  "batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
@@ -520,6 +521,25 @@ def library_full_fdfir(x, h, t_chunk=5):
         Hz = torch.fft.fft(h[z0:z0 + t_chunk], n=nfft)
         out[z0:z0 + t_chunk] = torch.fft.ifft(X[None, :] * Hz)[:, :n].abs().square()
     return out
+
+
+def bench_fdfir(fd, h, dev, xd, reps=5):
+    """Full-length FD-FIR (Eq. 2) through the library's own four-step kernels
+    (fdas_fdfir_convolve): 2^23-point transforms of the whole array per template."""
+    import torch
+    n, m = xd.numel(), h.shape[0]
+    out = torch.empty((m, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with fd.FdFir(h, n_max=n) as ff:
+        ff.convolve(xd, out, stream)
+        ms = _events_ms(lambda: ff.convolve(xd, out, stream), reps, stream)
+        length = ff.length
+    del out
+    torch.cuda.empty_cache()
+    return {"what": f"fdas_fdfir_convolve: {length}-point four-step transforms (2048 x {length // 2048}) of the "
+                    f"whole array, one inverse per template, same array and templates",
+            "ms_per_array": ms, "arrays_per_s": 1e3 / ms, "gpu_launches_per_array": 2 + 2 * m,
+            "spectra_bytes": 8 * m * length}
 
 
 def bench_library_fdfir(h, dev, xd, reps=3):

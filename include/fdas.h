@@ -233,6 +233,30 @@ int fdas_convolve_batch_noalloc(fdas_plan p, int count, const void *const *ins, 
  */
 int fdas_plan_status(fdas_plan p, void *stream);
 
+/*
+ * Full-length frequency-domain FIR (Eq. 2; the "naive FDFIR" of Sec. 3.2.1 and Table 1), the
+ * alternative the paper weighs overlap-save against: y_z = IFFT_P(FFT_P(x) . FFT_P(h_z)) with
+ * P the smallest power of two >= n_max + tpl_len - 1 (at least 2^21, at most 2^23), then
+ * |y_z[i]|^2 for i < n -- the same plane as fdas_convolve (Eq. 1), computed with P-point
+ * transforms of the whole array (four-step, P = 2048 x P/2048) instead of segments.
+ *
+ * fdas_fdfir_create: synchronous; copies the M x K complex64 templates (host, row-major) and
+ *   stores their P-point spectra on the current device (M x P x 8 bytes: 5.7 GB for 85
+ *   templates at P = 2^23).  Errors: INVALID_ARG (null pointers, sizes < 1, n_max + tpl_len - 1
+ *   > 2^23), OOM, CUDA.
+ * fdas_fdfir_length: *P = the transform length.
+ * fdas_fdfir_convolve: enqueues on `stream` (2 + 2M kernel launches) the plane out[z][i]
+ *   (float32, [M][n] row-major, device) of in[0, n) (complex64, device, 8-byte aligned);
+ *   1 <= n <= n_max; in and out must not overlap.  Calls on one plan share its scratch and
+ *   must not overlap on the GPU.  Errors: INVALID_ARG, CUDA.
+ * fdas_fdfir_destroy: frees the plan (the caller has synchronised its streams).
+ */
+typedef struct fdas_fdfir_s *fdas_fdfir;
+int fdas_fdfir_create(fdas_fdfir *out, int64_t n_max, const void *templates_c64_host, int n_templates, int tpl_len);
+int fdas_fdfir_length(fdas_fdfir f, int64_t *P);
+int fdas_fdfir_convolve(fdas_fdfir f, const void *in_c64_dev, int64_t n, float *out_power_dev, void *stream);
+int fdas_fdfir_destroy(fdas_fdfir f);
+
 /* ------------------------------------------------------------------------------------
  * Served form: continuous batching over one plan.
  *

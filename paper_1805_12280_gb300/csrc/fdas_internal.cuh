@@ -133,6 +133,12 @@ cudaError_t launch_td_direct(const float2 *x, int64_t n, const float2 *h, int M,
 
 // Plan-time kernels (FP64).
 cudaError_t launch_twiddles(int L, double2 *w64, float2 *w32, cudaStream_t s);
+// Full-length FD-FIR passes (P = 2048 * P2): forward transform of in[0, len) into A (times
+// scale); inverse of X . H into the power row out[0, n) through the scratch B.
+cudaError_t fdfir_forward(int P2, const float2 *in, int64_t len, const float2 *tw1, const float2 *tw2, float2 *A,
+                          float scale, cudaStream_t s);
+cudaError_t fdfir_inverse(int P2, const float2 *X, const float2 *H, float2 *B, const float2 *tw1, const float2 *tw2,
+                          float *out, int64_t n, cudaStream_t s);
 cudaError_t launch_pretransform(int L, const float2 *h32, int M, int K, const double2 *w64,
                                 float4 *Hperm, cudaStream_t s);
 

@@ -84,6 +84,52 @@ __device__ __forceinline__ void forward_fft(const float2 *src, float2 *e1, float
     if constexpr (GC == 2) dft<R, -1, 1, R>(X);
 }
 
+// Inverse L-point FFT (unnormalised, exp(+2 pi i nk / L)) by the NT = L/16 threads of a
+// block, from the C distribution the forward transform leaves (slot j of thread t holds
+// X[freq_of_slot(L, t, j)]) to natural order: on return v[a] = y[a*NT + t].  Passes C', B', A'
+// with conjugate twiddles read from the table; e1 and e2 must be free on entry (a barrier
+// after their last use) and are in use until the caller's next barrier.
+template <int L>
+__device__ __forceinline__ void inverse_fft(float2 (&v)[16], float2 *e1, float2 *e2, const float2 *__restrict__ tw)
+{
+    using Gm = Geo<L>;
+    constexpr int NT = Gm::NT, Q = Gm::Q, R = Gm::R, GB = Gm::GB, GC = Gm::GC, LD2 = Gm::LD2;
+    constexpr int MASK = L - 1;
+    const int tid = threadIdx.x, k1 = tid & 15, hi = tid >> 4;
+    // ---- pass C': R-point IDFT over k3, twiddle conj W_{QR}^{c k2}; exchange through e1
+    dft<R, 1, 1, 0>(v);
+    if constexpr (GC == 2) dft<R, 1, 1, R>(v);
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        const int k2 = hi + (NT / 16) * g;
+#pragma unroll
+        for (int c = 0; c < R; ++c)
+            e1[k1 + 16 * k2 + 16 * Q * c] = (c == 0) ? v[g * R] : cmul(v[g * R + c], cconj(__ldg(&tw[(16 * c * k2) & MASK])));
+    }
+    __syncthreads();
+    // ---- pass B': Q-point IDFT over k2, twiddle conj W_L^{(bR + c) k1}; exchange through e2
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[g * Q + k2] = e1[k1 + 16 * k2 + 16 * Q * cg];
+    }
+    dft<Q, 1, 1, 0>(v);
+    if constexpr (GB == 2) dft<Q, 1, 1, Q>(v);
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+        const int cg = hi + (NT / 16) * g;
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+            e2[(b * R + cg) + LD2 * k1] = cmul(v[g * Q + b], cconj(__ldg(&tw[((b * R + cg) * k1) & MASK])));
+    }
+    __syncthreads();
+    // ---- pass A': 16-point IDFT over k1 -> natural order
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = e2[tid + LD2 * k];
+    dft<16, 1>(v);
+}
+
 // The segment in e1.
 template <int L>
 __device__ __forceinline__ void forward_fft(float2 *e1, float2 *e2, const float2 *__restrict__ tw, float2 (&v)[16],

@@ -93,6 +93,10 @@ SIGNATURES = {
     "fdas_server_reset_stats": (_I, [_P]),
     "fdas_server_destroy": (_I, [_P]),
     "fdas_destroy": (_I, [_P]),
+    "fdas_fdfir_create": (_I, [ctypes.POINTER(_P), _I64, _P, _I, _I]),
+    "fdas_fdfir_length": (_I, [_P, ctypes.POINTER(_I64)]),
+    "fdas_fdfir_convolve": (_I, [_P, _P, _I64, _P, _P]),
+    "fdas_fdfir_destroy": (_I, [_P]),
     "fdas_strerror": (ctypes.c_char_p, [_I]),
     "fdas_last_error": (ctypes.c_char_p, []),
     "fdas_version": (ctypes.c_char_p, []),
@@ -242,6 +246,27 @@ def fdas_version() -> str:
     return load().fdas_version().decode()
 
 
+def fdas_fdfir_create(n_max: int, templates_ptr: int, n_templates: int, tpl_len: int) -> int:
+    h = _P()
+    _check(load().fdas_fdfir_create(ctypes.byref(h), int(n_max), _P(templates_ptr), int(n_templates), int(tpl_len)),
+           "fdas_fdfir_create")
+    return h.value
+
+
+def fdas_fdfir_length(plan: int) -> int:
+    p = _I64()
+    _check(load().fdas_fdfir_length(_P(plan), ctypes.byref(p)), "fdas_fdfir_length")
+    return p.value
+
+
+def fdas_fdfir_convolve(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().fdas_fdfir_convolve(_P(plan), _P(in_ptr), int(n), _P(out_ptr), _P(stream)), "fdas_fdfir_convolve")
+
+
+def fdas_fdfir_destroy(plan: int) -> None:
+    _check(load().fdas_fdfir_destroy(_P(plan)), "fdas_fdfir_destroy")
+
+
 # ---- convenience wrapper for torch tensors ---------------------------------
 
 def _stream_handle(stream) -> int:
@@ -353,6 +378,38 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class FdFir:
+    """Full-length frequency-domain FIR (Eq. 2) over the same template bank: P-point transforms
+    of the whole array, P = fdas_fdfir_length (the comparison the paper draws with overlap-save)."""
+
+    def __init__(self, templates, n_max: int):
+        t = np.ascontiguousarray(np.atleast_2d(templates), dtype=np.complex64)
+        self.n_templates, self.tpl_len = t.shape
+        self.handle = fdas_fdfir_create(n_max, t.ctypes.data, self.n_templates, self.tpl_len)
+        self.length = fdas_fdfir_length(self.handle)
+
+    def convolve(self, x, out=None, stream=None):
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        n = x.numel()
+        if out is None:
+            out = torch.empty((self.n_templates, n), dtype=torch.float32, device=x.device)
+        fdas_fdfir_convolve(self.handle, x.data_ptr(), n, out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def close(self) -> None:
+        if self.handle:
+            fdas_fdfir_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Server:

@@ -1,7 +1,7 @@
 """Seeded synthetic Fourier-domain input arrays shaped like the paper's workload.
 
 The FT-convolution module receives 2^22 complex single-precision Fourier bins per
-dedispersion trial (Sec. 3).  No survey data ship with the paper, so arrays are
+dedispersion trial (Sec. 3).  No telescope data ship with the paper, so arrays are
 synthesised:
 
   1. real series  s[n] = g[n] + sum_c a_c cos(2 pi (r_c u + z_c u^2 / 2)),

@@ -58,6 +58,12 @@ def test_argument_errors_without_gpu(lib):
     assert lib.fdas_convolve(None, None, 10, None, None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_destroy(None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_plan_tpl_per_cta(None, 10) == fd.fdas.FDAS_ERR_INVALID_ARG
+    assert lib.fdas_fdfir_convolve(None, None, 10, None, None) == fd.fdas.FDAS_ERR_INVALID_ARG
+    assert lib.fdas_fdfir_destroy(None) == fd.fdas.FDAS_ERR_INVALID_ARG
+    ff = ctypes.c_void_p()
+    assert lib.fdas_fdfir_create(ctypes.byref(ff), (1 << 23) - 419, ctypes.c_void_p(1), 85, 421) == \
+        fd.fdas.FDAS_ERR_INVALID_ARG                    # n_max + K - 1 > 2^23
+    assert lib.fdas_fdfir_create(ctypes.byref(ff), 100, None, 85, 421) == fd.fdas.FDAS_ERR_INVALID_ARG
     h = ctypes.c_void_p()
     opts = fd.fdas.fdas_opts(3000, 0, 0, 0)
     assert lib.fdas_plan_create(ctypes.byref(h), 100, ctypes.c_void_p(1), 85, 421, ctypes.byref(opts)) == \
