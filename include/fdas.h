@@ -234,6 +234,15 @@ int fdas_convolve_batch_noalloc(fdas_plan p, int count, const void *const *ins, 
 int fdas_plan_status(fdas_plan p, void *stream);
 
 /*
+ * Failure-detection self-test: enqueues on `stream` one block whose bounded mbarrier wait
+ * runs out after limit_ms (0 < limit_ms <= 1000) because it waits for a copy that is never
+ * issued -- the path a segment kernel takes when a TMA load never lands.  The block sets the
+ * plan's status word and exits; no copy is in flight and the context stays usable.  The next
+ * fdas_plan_status returns FDAS_ERR_TIMEOUT (and clears the word).  Errors: INVALID_ARG, CUDA.
+ */
+int fdas_selftest_wait_timeout(fdas_plan p, double limit_ms, void *stream);
+
+/*
  * Full-length frequency-domain FIR (Eq. 2; the "naive FDFIR" of Sec. 3.2.1 and Table 1), the
  * alternative the paper weighs overlap-save against: y_z = IFFT_P(FFT_P(x) . FFT_P(h_z)) with
  * P the smallest power of two >= n_max + tpl_len - 1 (at least 2^21, at most 2^23), then

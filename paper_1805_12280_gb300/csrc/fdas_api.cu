@@ -620,6 +620,7 @@ int validate_array(fdas_plan p, const void *in, int64_t n, const float *out)
 
 int plan_templates(fdas_plan p) { return p ? p->M : 0; }
 int plan_grouped(fdas_plan p) { return p && p->d_rows ? 1 : 0; }
+int *plan_status_word(fdas_plan p) { return p ? p->d_status : nullptr; }
 int64_t plan_n_max(fdas_plan p) { return p ? p->n_max : 0; }
 
 // Plan accessor and error reporting for code outside this file.

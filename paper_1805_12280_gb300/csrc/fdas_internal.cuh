@@ -107,6 +107,7 @@ void lane_free(Lane *l);
 int validate_array(fdas_plan p, const void *in, int64_t n, const float *out);
 int plan_templates(fdas_plan p);
 int plan_grouped(fdas_plan p);
+int *plan_status_word(fdas_plan p);   // the plan's device status word
 int64_t plan_n_max(fdas_plan p);
 
 // Graph-free launches of the persistent batch kernel with caller-provided work counters

@@ -85,6 +85,7 @@ SIGNATURES = {
     "fdas_convolve_direct": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_convolve_batch_noalloc": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P), _P]),
     "fdas_plan_status": (_I, [_P, _P]),
+    "fdas_selftest_wait_timeout": (_I, [_P, ctypes.c_double, _P]),
     "fdas_server_create": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(fdas_server_opts)]),
     "fdas_server_submit": (_I, [_P, _P, _I64, ctypes.POINTER(_I64)]),
     "fdas_server_wait": (_I, [_P, _I64, _I64, ctypes.POINTER(_P)]),
@@ -155,6 +156,10 @@ def fdas_plan_tpl_per_cta(plan: int, n: int) -> int:
     g = load().fdas_plan_tpl_per_cta(_P(plan), int(n))
     _check(min(g, 0), "fdas_plan_tpl_per_cta")
     return g
+
+
+def fdas_selftest_wait_timeout(plan: int, limit_ms: float, stream: int = 0) -> None:
+    _check(load().fdas_selftest_wait_timeout(_P(plan), float(limit_ms), _P(stream)), "fdas_selftest_wait_timeout")
 
 
 def fdas_convolve(plan: int, in_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:

@@ -58,6 +58,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.fdas_convolve(None, None, 10, None, None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_destroy(None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_plan_tpl_per_cta(None, 10) == fd.fdas.FDAS_ERR_INVALID_ARG
+    assert lib.fdas_selftest_wait_timeout(None, 1.0, None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_fdfir_convolve(None, None, 10, None, None) == fd.fdas.FDAS_ERR_INVALID_ARG
     assert lib.fdas_fdfir_destroy(None) == fd.fdas.FDAS_ERR_INVALID_ARG
     ff = ctypes.c_void_p()

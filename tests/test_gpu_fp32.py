@@ -180,3 +180,18 @@ def test_plane_pointer_alignment_paths(fd, bank):
             fd.fdas_convolve(plan.handle, x.data_ptr(), n, buf.data_ptr() + 4 * shift)
             plan.status()
             assert torch.equal(buf[shift:shift + m * n].view(m, n), ref)
+
+
+def test_bounded_wait_timeout_is_reported(fd, oracle_mod, bank):
+    # a wait for a copy that is never issued runs out after 5 ms: the status word reports it
+    # once, and the context and the plan stay usable
+    x = synth.make_input(synth.single_small(n=3000, seed=14))
+    with fd.Plan(bank[:3], n_max=x.size) as plan:
+        plan.status()
+        fd.fdas_selftest_wait_timeout(plan.handle, 5.0)
+        with pytest.raises(fd.FdasError) as e:
+            plan.status()
+        assert e.value.code == fd.fdas.FDAS_ERR_TIMEOUT
+        plan.status()                                    # read and cleared
+        p = _run(fd, plan, x)
+    compare(p, oracle_mod.direct_power(x, bank[:3]), TOL_FP32)

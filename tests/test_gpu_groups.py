@@ -70,17 +70,20 @@ def test_shifted_supports_ragged_lengths(fd, oracle_mod, n):
             assert np.all(p[z, :min(first[z], n)] == 0.0)
 
 
-def test_candidates_equal_thresholded_plane(fd, bank):
-    x = synth.make_input(synth.single_small(n=30000, seed=41))
+@pytest.mark.parametrize("n,threshold", [(30000, THRESHOLD), (3000, -1.0)])
+def test_candidates_equal_thresholded_plane(fd, bank, n, threshold):
+    # T < 0 also selects the zero outputs before each template's first tap
+    x = synth.make_input(synth.single_small(n=n, seed=41))
     xd = torch.from_numpy(x).cuda()
     with fd.Plan(bank, n_max=1 << 22, group_support=1) as plan:
         plane = plan.convolve(xd).cpu().numpy()
-        buf, count = plan.candidates(xd, threshold=THRESHOLD)
+        buf, count = plan.candidates(xd, threshold=threshold, max_cand=85 * n + 16)
         plan.status()
         got = fd.candidates_to_numpy(buf, count)
     got = got[np.lexsort((got["bin"], got["tpl"]))]
-    zi, ii = np.nonzero(plane > THRESHOLD)
+    zi, ii = np.nonzero(plane > threshold)
     assert int(count.item()) == zi.size > 100
+    assert threshold > 0 or zi.size == 85 * n
     np.testing.assert_array_equal(got["tpl"], zi)
     np.testing.assert_array_equal(got["bin"], ii)
     np.testing.assert_array_equal(got["power"], plane[zi, ii])
