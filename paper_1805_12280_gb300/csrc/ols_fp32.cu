@@ -298,10 +298,14 @@ __device__ __forceinline__ bool run_item(Block<L> &B, const OlsArgs &a, const CU
             v[2 * jp + 1] = cmul(v[2 * jp + 1], make_float2(h.z, h.w));
         }
         // ---- inverse pass C': R-point IDFT over k3, twiddle conj W_{QR}^{c k2}
+        uint32_t t1r[32];   // the C' twiddles come back from TMEM during the radix-R DFTs
+        tmem_ld32_issue(my + kColTw1, t1r);
         dft<R, 1, 1, 0>(v);
         if constexpr (GC == 2) dft<R, 1, 1, R>(v);
+        tmem_ld32_wait(t1r);
         float2 tw1[16];
-        tmem_ld_c16(my + kColTw1, tw1);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tw1[j] = make_float2(__uint_as_float(t1r[2 * j]), __uint_as_float(t1r[2 * j + 1]));
         if constexpr (GC == 2) {
             // the thread's two k2 values (hi and hi + Q/2) of each c share one 16-byte slot:
             // k1 + 16 (k2 mod Q/2) + 8 Q c; pass B' reads both halves with one load
