@@ -5,12 +5,13 @@
 //   1. TMA loads the L-point segment x[s*S - (K-1) .. s*S - (K-1) + L) into shared
 //      memory; the tensor map zero-fills before 0 (the K-1 leading zeros of the first
 //      segment) and past n;
-//   2. forward FFT (passes A, B, C; two shared-memory exchanges), the spectrum stays
-//      in registers for the whole template loop;
+//   2. forward FFT (passes A, B, C; two shared-memory exchanges); the spectrum waits in
+//      the thread's TMEM lane for the whole template loop;
 //   3. per template: element-wise product with the pre-transformed template (prefetched
-//      two templates ahead into a shared-memory double buffer by cp.async.bulk), inverse
-//      FFT (passes C', B', A'; two exchanges; 1/L is folded into the template), discard
-//      of the first K-1 points, |y|^2, coalesced stores of the valid S points.
+//      by cp.async.bulk into shared memory, one template ahead in a single buffer at
+//      L = 2048 and 4096, two ahead in a double buffer at L = 1024), inverse FFT (passes
+//      C', B', A'; two exchanges; 1/L is folded into the template), discard of the first
+//      K-1 points, |y|^2, coalesced stores of the valid S points.
 // ols_fp32_kernel runs one item per block (grid = segments x groups of one array);
 // ols_fp32_batch is persistent: resident blocks pull items of many arrays from a
 // device work counter.
@@ -87,7 +88,7 @@ template <int L>
 struct Block {
     float2 *e1;      // segment, then exchange buffer 1 [L]
     float2 *e2;      // exchange buffer 2 [16][NT + 1]
-    float4 *hb;      // template double buffer [2][8][NT]
+    float4 *hb;      // template buffer(s) [hbuf<L>()][8][NT]
     uint64_t *bar;   // [0] segment, [1], [2] template buffers
     uint32_t *tslot; // TMEM base address written by the allocating warp
     uint32_t tmem = 0;
