@@ -695,13 +695,39 @@ KERNEL_SOURCES = {"fp32": ("ols_fp32.cu", "ols_common.cuh", "fft_regs.cuh", "ptx
                   "tc": ("ols_tc.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "fdas_internal.cuh")}
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and blank space (string literals kept as they are),
+    so that an edit of the comments alone does not invalidate a traffic record."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':                                   # string literal, escapes included
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_sources_sha256(precision: str) -> str:
+    """Hash of the code (comments and layout excluded) of the sources a segment kernel is
+    compiled from: a committed traffic record is used only while it matches."""
     import hashlib
     src = os.path.join(ROOT, "paper_1805_12280_gb300", "csrc")
     h = hashlib.sha256()
     for fn in KERNEL_SOURCES[precision]:
-        with open(os.path.join(src, fn), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(src, fn), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()
 
 
