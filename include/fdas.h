@@ -119,7 +119,8 @@ int fdas_plan_tpl_per_cta(fdas_plan p, int64_t n);
  *   out_power_dev : device pointer, float32 [M][n] row-major, 4-byte aligned; every
  *                   element is written.  Must not overlap the input.
  *
- * Enqueues one kernel launch on `stream` and returns without waiting.  Per segment
+ * Enqueues one kernel launch on `stream` (one per template group for a plan created
+ * with group_support) and returns without waiting.  Per segment
  * of L points (step S, preceded by K-1 zeros for the first, zero-filled past n):
  * one forward FFT, then for each template the element-wise product, the inverse
  * FFT, the discard of the first K-1 points and the power (Algorithm 2, Sec. 4.3).
@@ -173,8 +174,9 @@ int fdas_convolve_candidates(fdas_plan p, const void *in_c64_dev, int64_t n, flo
  *
  * Synchronous: copies the input to plan-owned device staging memory (allocated on
  * the first call, sized for n_max), runs the segment kernel in chunks and copies
- * each finished chunk of the plane back while the next one is computed, and
- * returns once out_power_host is complete.  Errors: INVALID_ARG, OOM, CUDA.
+ * each finished chunk of the plane back while the next one is computed (a grouped
+ * plan: all launches, then one copy), and returns once out_power_host is complete.
+ * Errors: INVALID_ARG, OOM, CUDA.
  */
 int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *out_power_host,
                        void *stream);
@@ -190,11 +192,12 @@ int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *o
  * Enqueues, per group of up to 120 arrays, one replay of the plan's CUDA graph
  * [reset the work counter -> persistent kernel with one block per resident slot]; the
  * kernel's blocks take work items (array, template group, segment) from the counter.
- * Items are identical to fdas_convolve's, so results equal those of fdas_convolve on
- * each array.  Asynchronous.  Calls on one plan are serialised by the library on the
+ * Each template's arithmetic is that of fdas_convolve (whatever the templates per block),
+ * so results equal those of fdas_convolve on each array bit for bit.  Asynchronous.  Calls on one plan are serialised by the library on the
  * host; their kernels run in stream order and must not overlap in time: do not
  * issue batches of one plan on two streams that run concurrently.
- * Errors: INVALID_ARG (any entry invalid: nothing is enqueued), CUDA.
+ * Errors: INVALID_ARG (any entry invalid: nothing is enqueued), UNSUPPORTED (a plan
+ * created with group_support), CUDA.
  */
 int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns,
                         float *const *outs, void *stream);
