@@ -56,7 +56,7 @@ def test_bank_is_split_and_matches_eq1(fd, oracle_mod, bank):
 def test_shifted_supports_ragged_lengths(fd, oracle_mod, n):
     h = _windowed_bank(n)
     x = _rand(n, n + 1)
-    for L in (1024, 2048):
+    for L in (1024, 2048, 4096):
         with fd.Plan(h, n_max=max(n, 40000), seg_len=L, tpl_per_cta=5, group_support=1) as plan:
             assert 1 <= plan.desc.groups <= 6
             out = torch.full((h.shape[0], n), -1.0, device="cuda")
