@@ -9,8 +9,34 @@
 
 namespace fdas {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract as one packed FP32x2 instruction each (sm_100 family): both
+// lanes round exactly as two scalar operations would.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+// a + S i b for S = +-1, in scalar form: the lane swap of i b would cost moves in packed form.
+template <int S>
+__device__ __forceinline__ float2 cadd_i(float2 a, float2 b)
+{
+    return S > 0 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -72,12 +98,25 @@ __device__ __forceinline__ void dft2(float2 &a0, float2 &a1)
 template <int DIR>
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
 {
-    float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-    float2 t2 = cadd(a1, a3), t3 = twc<1, 4, DIR>(csub(a1, a3));
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    const float2 t2 = cadd(a1, a3), d = csub(a1, a3);   // the odd part, times DIR i below
     a0 = cadd(t0, t2);
     a2 = csub(t0, t2);
-    a1 = cadd(t1, t3);
-    a3 = csub(t1, t3);
+    a1 = cadd_i<DIR>(t1, d);
+    a3 = cadd_i<-DIR>(t1, d);
+}
+
+// dft4 whose third input enters multiplied by DIR i (the exp(DIR i pi/2) twiddle of a
+// radix-16 column): a2 is passed untwiddled.
+template <int DIR>
+__device__ __forceinline__ void dft4_i2(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+{
+    const float2 t0 = cadd_i<DIR>(a0, a2), t1 = cadd_i<-DIR>(a0, a2);
+    const float2 t2 = cadd(a1, a3), d = csub(a1, a3);
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd_i<DIR>(t1, d);
+    a3 = cadd_i<-DIR>(t1, d);
 }
 
 namespace detail {
@@ -108,11 +147,11 @@ struct Dft<8, DIR, ST, OFF> {
         dft4<DIR>(e0, e1, e2, e3);
         dft4<DIR>(o0, o1, o2, o3);
         o1 = twc<1, 8, DIR>(o1);
-        o2 = twc<2, 8, DIR>(o2);
         o3 = twc<3, 8, DIR>(o3);
         v[OFF + 0 * ST] = cadd(e0, o0); v[OFF + 4 * ST] = csub(e0, o0);
         v[OFF + 1 * ST] = cadd(e1, o1); v[OFF + 5 * ST] = csub(e1, o1);
-        v[OFF + 2 * ST] = cadd(e2, o2); v[OFF + 6 * ST] = csub(e2, o2);
+        // o2 enters times exp(DIR i pi/2) = DIR i
+        v[OFF + 2 * ST] = cadd_i<DIR>(e2, o2); v[OFF + 6 * ST] = cadd_i<-DIR>(e2, o2);
         v[OFF + 3 * ST] = cadd(e3, o3); v[OFF + 7 * ST] = csub(e3, o3);
     }
 };
@@ -135,14 +174,14 @@ struct Dft<16, DIR, ST, OFF> {
         a[1][2] = twc<2, 16, DIR>(a[1][2]);
         a[1][3] = twc<3, 16, DIR>(a[1][3]);
         a[2][1] = twc<2, 16, DIR>(a[2][1]);
-        a[2][2] = twc<4, 16, DIR>(a[2][2]);
-        a[2][3] = twc<6, 16, DIR>(a[2][3]);
+        a[2][3] = twc<6, 16, DIR>(a[2][3]);   // a[2][2] enters times DIR i inside dft4_i2
         a[3][1] = twc<3, 16, DIR>(a[3][1]);
         a[3][2] = twc<6, 16, DIR>(a[3][2]);
         a[3][3] = twc<9, 16, DIR>(a[3][3]);
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
-            dft4<DIR>(a[0][k1], a[1][k1], a[2][k1], a[3][k1]);
+            if (k1 == 2) dft4_i2<DIR>(a[0][k1], a[1][k1], a[2][k1], a[3][k1]);
+            else dft4<DIR>(a[0][k1], a[1][k1], a[2][k1], a[3][k1]);
             v[OFF + (k1 + 0) * ST] = a[0][k1];
             v[OFF + (k1 + 4) * ST] = a[1][k1];
             v[OFF + (k1 + 8) * ST] = a[2][k1];
