@@ -106,7 +106,8 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates_c64_ho
 int fdas_plan_describe(fdas_plan p, fdas_plan_desc *desc);
 
 /* Templates per thread block that fdas_convolve uses for an array of n points (the plan's
- * fixed G, or the per-call choice when the plan was created with tpl_per_cta = 0).
+ * fixed G, or the per-call choice when the plan was created with tpl_per_cta = 0; a grouped
+ * plan applies the same rule to each template group and its segment count).
  * Returns G >= 1, or a negative error code (INVALID_ARG for a null plan or n outside
  * [1, n_max]).  Host only; no CUDA call. */
 int fdas_plan_tpl_per_cta(fdas_plan p, int64_t n);
