@@ -40,9 +40,9 @@ extern "C" {
 
 /* Arithmetic forms of the segment FFTs. */
 #define FDAS_PREC_FP32          0     /* FP32 CUDA-core FFTs (default) */
-#define FDAS_PREC_TC_FP16       1     /* tensor-core DFT-GEMM stages for the inverse FFT's radix-16
-                                         passes: fp16 data, fp16 hi/lo-split DFT matrices, FP32
-                                         accumulation; needs seg_len 2048 */
+#define FDAS_PREC_TC_FP16       1     /* the inverse FFT's first radix-16 pass as a tensor-core
+                                         DFT-GEMM: fp16 data, fp16 hi/lo-split DFT matrix, FP32
+                                         accumulation; the other passes FP32; needs seg_len 2048 */
 
 typedef struct fdas_plan_s *fdas_plan;
 

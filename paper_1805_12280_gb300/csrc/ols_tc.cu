@@ -1,14 +1,15 @@
 // Tensor-core form of the overlap-save segment kernel (L = 2048).
 //
-// Same work item and forward FFT as the FP32 kernel.  Per template, the inverse FFT's two
-// radix-16 passes (B' over k2, A' over k1) are dense DFT-matrix GEMMs on the 5th-generation
-// tensor cores: each pass is D[128 x 32] = A[128 x 32] . W[32 x 32] with the complex
-// 16-point inverse DFT written as a real 32 x 32 matrix, A = the 128 sub-transform rows of
-// one template's data in fp16 (staged in shared memory), W split into fp16 hi + lo parts
-// (two MMAs per K-step recover the DFT matrix to ~2^-22), FP32 accumulation in tensor
-// memory.  The product with H_z, the radix-8 pass C', the inter-pass twiddles, the discard
-// and |y|^2 stay on the CUDA cores in FP32.  B' uses W/16 and A' uses 16 W (exact power-of-2
-// scalings) so that the fp16 operand of A' stays far from the fp16 range limit.
+// Same work item, TMA segment load, template prefetch and forward FFT as the FP32 kernel.
+// Per template, the inverse FFT's radix-16 pass B' (over k2) is a dense DFT-matrix GEMM on the
+// 5th-generation tensor cores: D[128 x 32] = A[128 x 32] . W[32 x 32], the complex 16-point
+// inverse DFT written as a real 32 x 32 matrix, A = the 128 sub-transform rows of one
+// template's data in fp16 (written by the threads into shared memory), W split into fp16 hi +
+// lo parts (two MMAs per K-step recover the DFT matrix to ~2^-22), FP32 accumulation in tensor
+// memory.  The product with H_z, the radix-8 pass C', the twiddles, the last radix-16 pass A'
+// (packed FP32x2 butterflies), the discard and |y|^2 stay on the CUDA cores in FP32, so each
+// template's data is rounded to fp16 once.  B' uses W/16 (an exact power of 2 that keeps the
+// MMA operands' products far from the fp16 range limit); the B' twiddles carry the factor 16.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -32,21 +33,25 @@ constexpr uint32_t A_BYTES = 16 * A_SBO;                // 10240
 constexpr uint32_t B_LBO = 128, B_SBO = 512, B_BYTES = 4 * B_SBO;   // 2048 per matrix
 constexpr uint32_t W_BYTES = 4 * B_BYTES;               // B' hi, B' lo, A' hi, A' lo
 constexpr uint32_t H_BYTES = sizeof(float2) * L;
-// TMEM columns: D of B' [0, 32), D of A' [32, 64), this thread's segment spectrum [64, 96)
-// and C' twiddles [96, 128) (kept there instead of registers).
-constexpr uint32_t TMEM_COLS = 128, COL_DB = 0, COL_DA = 32, COL_X = 64, COL_TW1 = 96;
+// TMEM columns: D of B' [0, 32), this thread's segment spectrum [32, 64), C' twiddles
+// [64, 96) and B' twiddles (times 16) [96, 128), kept there instead of registers.
+constexpr uint32_t TMEM_COLS = 128, COL_DB = 0, COL_X = 32, COL_TW1 = 64, COL_TW2 = 96;
 // kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
 constexpr uint32_t IDESC = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t WB_BYTES = 2 * B_BYTES;                // the B' matrices (hi, lo) in the block
 
+// 53.5 KB per block, so that four blocks share an SM: the segment buffer is the forward FFT's
+// first exchange and then the A operand of B'; one template buffer, refilled one ahead.
 struct Smem {
-    static constexpr size_t e1 = 0;                                  // segment / B' A-operand
-    static constexpr size_t e2 = e1 + sizeof(float2) * L;            // exchange / A' A-operand
-    static constexpr size_t hb = e2 + sizeof(float2) * 16 * LD2;     // template double buffer
-    static constexpr size_t wm = (hb + 2 * H_BYTES + 127) & ~size_t(127);
-    static constexpr size_t bar = wm + W_BYTES;                      // 5 mbarriers
-    static constexpr size_t slot = bar + 5 * 8;                      // TMEM address
+    static constexpr size_t e1 = 0;                                  // segment / exchange 1 / A of B'
+    static constexpr size_t e2 = e1 + sizeof(float2) * L;            // exchange 2 (forward, A')
+    static constexpr size_t hb = e2 + sizeof(float2) * 16 * LD2;     // template buffer
+    static constexpr size_t wm = hb + H_BYTES;                       // B' hi, B' lo
+    static constexpr size_t bar = wm + WB_BYTES;                     // [0] segment+W, [1] template, [2] B' MMA
+    static constexpr size_t slot = bar + 3 * 8;                      // TMEM address
     static constexpr size_t total = 128 + slot + 16;
-    static_assert(sizeof(float2) * L >= A_BYTES && sizeof(float2) * 16 * LD2 >= A_BYTES, "operand aliasing");
+    static_assert(sizeof(float2) * L >= A_BYTES, "A operand fits the segment buffer");
+    static_assert(hb % 128 == 0 && wm % 16 == 0, "bulk copy alignment");
 };
 
 __host__ __device__ inline uint32_t a_off(int r, int k)
@@ -121,21 +126,21 @@ __global__ void tc_matrix_kernel(unsigned char *out)
 }  // namespace tc
 
 #ifndef FDAS_TC_MINB
-#define FDAS_TC_MINB 3
+#define FDAS_TC_MINB 4
 #endif
 __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     ols_tc_kernel(const __grid_constant__ CUtensorMap tmap, const OlsArgs a, const unsigned char *__restrict__ wmat)
 {
     using namespace tc;
+    constexpr int MASK = L - 1;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float2 *e1 = reinterpret_cast<float2 *>(sm + Smem::e1);
     float2 *e2 = reinterpret_cast<float2 *>(sm + Smem::e2);
     float4 *hb = reinterpret_cast<float4 *>(sm + Smem::hb);
     unsigned char *wm = sm + Smem::wm;
-    unsigned char *aB = sm + Smem::e1;   // A operand of B' (aliases the segment buffer)
-    unsigned char *aA = sm + Smem::e2;   // A operand of A' (aliases exchange buffer 2)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Smem::bar);   // [0] segment+W, [1],[2] templates, [3] B' MMA, [4] A' MMA
+    unsigned char *aB = sm + Smem::e1;   // A operand of B' (the segment buffer, free after the forward FFT)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Smem::bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Smem::slot);
 
     const int tid = threadIdx.x, warp = tid >> 5, k1 = tid & 15, hi = tid >> 4;
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     const int z0 = blockIdx.y * a.G, z1 = min(z0 + a.G, a.M);
 
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -157,79 +162,79 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)) + W_BYTES);
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)) + WB_BYTES);
         const int c0 = seg * a.S - (a.K - 1);
 #pragma unroll
         for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, &bar[0]);
-        bulk_load(wm, wmat, W_BYTES, &bar[0]);
-        for (int i = 0; i < 2 && z0 + i < z1; ++i) {
-            mbar_arrive_expect_tx(&bar[1 + i], H_BYTES);
-            bulk_load(hb + i * 8 * NT, a.H + (size_t)(z0 + i) * 8 * NT, H_BYTES, &bar[1 + i]);
+        bulk_load(wm, wmat, WB_BYTES, &bar[0]);
+        if (z0 < z1) {
+            mbar_arrive_expect_tx(&bar[1], H_BYTES);
+            bulk_load(hb, a.H + (size_t)z0 * 8 * NT, H_BYTES, &bar[1]);
         }
     }
-    // Inverse twiddles: C' output (W_{QR}^{-c k2}, parked in TMEM) and B' output
-    // (W_L^{-(bR + c) k1}, registers).
+    // Inverse twiddles, fixed for this thread: C' output conj W_{QR}^{c k2} and B' output
+    // 16 conj W_L^{(bR + c) k1} (the 16 undoes the W/16 of the B' matrices), parked in TMEM.
     const uint32_t my = tmem + ((uint32_t)(warp * 32) << 16);
-    float2 tw2[16];
     {
-        float2 tw1[16];
+        float2 tw[16];
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             const int k2 = hi + 8 * g;
 #pragma unroll
-            for (int c = 0; c < R; ++c) tw1[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & (L - 1)]));
+            for (int c = 0; c < R; ++c) tw[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & MASK]));
         }
-        tmem_st_c16(my + COL_TW1, tw1);
-    }
+        tmem_st_c16(my + COL_TW1, tw);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) tw2[b] = cconj(__ldg(&a.tw[((b * R + hi) * k1) & (L - 1)]));
+        for (int b = 0; b < Q; ++b) {
+            const float2 w = __ldg(&a.tw[((b * R + hi) * k1) & MASK]);
+            tw[b] = make_float2(16.f * w.x, -16.f * w.y);
+        }
+        tmem_st_c16(my + COL_TW2, tw);
+    }
 
     const bool seg_ok = __syncthreads_and(mbar_wait_bounded(&bar[0], 0, kWaitLimitNs));
     bool ok = seg_ok;
-    // per-buffer counters as scalars (a runtime-indexed array would live in local memory)
-    uint32_t h_uses0 = 0, h_uses1 = 0, h_iss0 = z0 < z1, h_iss1 = z0 + 1 < z1;
-    uint32_t b_uses = 0, b_done = 0, a_uses = 0, a_done = 0;   // MMA completions awaited / seen
+    uint32_t h_uses = 0, h_iss = z0 < z1, b_uses = 0, b_done = 0;
     float2 v[16];
     if (ok) {
         float2 X[16];
         forward_fft<L>(e1, e2, a.tw, v, X);
         tmem_st_c16(my + COL_X, X);   // the spectrum waits in TMEM for the template loop
-        __syncthreads();   // e1/e2 are free: they become the A operands
+        __syncthreads();              // e1 is read: it becomes the A operand of B'
     }
     const int64_t seg_out = (int64_t)seg * a.S;
     const int64_t nvalid64 = a.n - seg_out;
     const unsigned nvalid = (unsigned)(nvalid64 < a.S ? nvalid64 : a.S);
     const int obase = tid - (a.K - 1);
-    const uint32_t aB_addr = smem_u32(aB), aA_addr = smem_u32(aA), w_addr = smem_u32(wm);
+    unsigned vmask = 0;   // bit j: register slot j of this thread holds a kept output
+#pragma unroll
+    for (int j = 0; j < 16; ++j) vmask |= ((unsigned)(j * NT + obase) < nvalid ? 1u : 0u) << j;
+    const uint32_t aB_addr = smem_u32(aB), w_addr = smem_u32(wm);
 
-    // Software pipeline over templates: the B' MMA of template z runs while the threads
-    // finish template z-1 (A' output, power, stores); the A' MMA of template z runs while
-    // they prepare template z+1 (product, C', B' operand).
-    float f[32];
     for (int z = z0; ok && z < z1; ++z) {
-        const int buf = (z - z0) & 1;
-        const float4 *hz = hb + buf * 8 * NT;
-        const bool h_ok = mbar_wait_bounded(&bar[1 + buf], (buf ? h_uses1 : h_uses0) & 1, kWaitLimitNs);
-        if (buf) h_uses1++; else h_uses0++;
-        // ---- S1(z): product with H_z, pass C' (radix 8, CUDA cores), twiddle, fp16 rows of B'
+        const bool h_ok = mbar_wait_bounded(&bar[1], h_uses & 1, kWaitLimitNs);
+        h_uses++;
+        // ---- product with H_z, pass C' (radix 8), twiddle, fp16 rows of the B' operand
         tmem_ld_c16(my + COL_X, v);
 #pragma unroll
         for (int jp = 0; jp < 8; ++jp) {
-            const float4 h = hz[jp * NT + tid];
+            const float4 h = hb[jp * NT + tid];
             v[2 * jp] = cmul(v[2 * jp], make_float2(h.x, h.y));
             v[2 * jp + 1] = cmul(v[2 * jp + 1], make_float2(h.z, h.w));
         }
         dft<R, 1, 1, 0>(v);
         dft<R, 1, 1, R>(v);
-        float2 tw1[16];
-        tmem_ld_c16(my + COL_TW1, tw1);
+        {
+            float2 tw1[16];
+            tmem_ld_c16(my + COL_TW1, tw1);
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            const int k2 = hi + 8 * g;
+            for (int g = 0; g < 2; ++g) {
+                const int k2 = hi + 8 * g;
 #pragma unroll
-            for (int c = 0; c < R; ++c) {
-                const float2 y = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
-                st_h2(aB, a_off(k1 + 16 * c, 2 * k2), y.x, y.y);   // row (k1, c), K pair k2
+                for (int c = 0; c < R; ++c) {
+                    const float2 y = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
+                    st_h2(aB, a_off(k1 + 16 * c, 2 * k2), y.x, y.y);   // row (k1, c), K pair k2
+                }
             }
         }
         fence_proxy_async_smem();
@@ -240,87 +245,54 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
         }
         if (tid == 0) {
             fence_after_sync();
-            // every thread has read hb[buf]: refill it with the template two ahead
-            if (z + 2 < z1) {
-                if (buf) h_iss1++; else h_iss0++;
-                mbar_arrive_expect_tx(&bar[1 + buf], H_BYTES);
-                bulk_load(hb + buf * 8 * NT, a.H + (size_t)(z + 2) * 8 * NT, H_BYTES, &bar[1 + buf]);
+            // every thread has read the template buffer: refill it with the next template
+            if (z + 1 < z1) {
+                h_iss++;
+                mbar_arrive_expect_tx(&bar[1], H_BYTES);
+                bulk_load(hb, a.H + (size_t)(z + 1) * 8 * NT, H_BYTES, &bar[1]);
             }
-            // ---- pass B'(z): D_B = A_B . (W_hi + W_lo) / 16 over K = 32 (two K-steps)
+            // ---- pass B': D_B = A_B . (W_hi + W_lo) / 16 over K = 32 (two K-steps)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 const uint64_t ad = smem_desc(aB_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
-                mma_f16(tmem, ad, smem_desc(w_addr + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
-                mma_f16(tmem, ad, smem_desc(w_addr + B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
+                mma_f16(tmem + COL_DB, ad, smem_desc(w_addr + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
+                mma_f16(tmem + COL_DB, ad, smem_desc(w_addr + B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
             }
-            mma_commit(&bar[3]);
+            mma_commit(&bar[2]);
         }
-        // ---- S3(z-1): A' output of the previous template -> discard, power, store
-        bool ma_ok = true;
-        if (z > z0) {
-            ma_ok = mbar_wait_bounded(&bar[4], a_uses & 1, kWaitLimitNs);
-            a_uses++;
-            a_done += ma_ok;
-            fence_after_sync();
-            tmem_ld_f32(my + COL_DA, f);
-            float *orow = a.out + (size_t)(z - 1) * (size_t)a.n + seg_out;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int o = j * NT + obase;
-                if ((unsigned)o < nvalid) orow[o] = fmaf(f[2 * j], f[2 * j], f[2 * j + 1] * f[2 * j + 1]);
-            }
-        }
-        // ---- S2(z): B' output row tid = (k1, c = tid / 16), columns (re, im) of b = 0..15
-        const bool mb_ok = mbar_wait_bounded(&bar[3], b_uses & 1, kWaitLimitNs);
+        const bool mb_ok = mbar_wait_bounded(&bar[2], b_uses & 1, kWaitLimitNs);
         b_uses++;
         b_done += mb_ok;
         fence_after_sync();
-        tmem_ld_f32(my + COL_DB, f);
+        // ---- B' output row tid = (k1, c = hi): b = 0..15, twiddle, exchange to A'
+        {
+            float f[32];
+            tmem_ld_f32(my + COL_DB, f);
+            float2 tw2[16];
+            tmem_ld_c16(my + COL_TW2, tw2);
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            const float2 y = cmul(make_float2(f[2 * b], f[2 * b + 1]), tw2[b]);
-            st_h2(aA, a_off(b * R + hi, 2 * k1), y.x, y.y);       // row t = bR + c, K pair k1
+            for (int b = 0; b < Q; ++b) e2[(b * R + hi) + LD2 * k1] = cmul(make_float2(f[2 * b], f[2 * b + 1]), tw2[b]);
         }
-        fence_proxy_async_smem();
-        fence_before_sync();
-        if (!__syncthreads_and(mb_ok && ma_ok)) {
+        fence_before_sync();   // the TMEM reads of D_B precede the next B' MMA
+        if (!__syncthreads_and(mb_ok)) {
             ok = false;
             break;
         }
-        if (tid == 0) {
-            fence_after_sync();
-            // ---- pass A'(z): D_A = A_A . 16 (W_hi + W_lo)
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t ad = smem_desc(aA_addr + ks * 2 * A_LBO, A_LBO, A_SBO);
-                mma_f16(tmem + COL_DA, ad, smem_desc(w_addr + 2 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), ks);
-                mma_f16(tmem + COL_DA, ad, smem_desc(w_addr + 3 * B_BYTES + ks * 2 * B_LBO, B_LBO, B_SBO), 1);
-            }
-            mma_commit(&bar[4]);
-        }
-    }
-    // ---- drain: A' output of the last template
-    if (ok && z1 > z0) {
-        const bool ma_ok = mbar_wait_bounded(&bar[4], a_uses & 1, kWaitLimitNs);
-        a_uses++;
-        a_done += ma_ok;
         fence_after_sync();
-        tmem_ld_f32(my + COL_DA, f);
-        float *orow = a.out + (size_t)(z1 - 1) * (size_t)a.n + seg_out;
+        // ---- pass A': 16-point IDFT over k1 -> natural order y[a*NT + t], power, stores
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int o = j * NT + obase;
-            if ((unsigned)o < nvalid) orow[o] = fmaf(f[2 * j], f[2 * j], f[2 * j + 1] * f[2 * j + 1]);
-        }
-        ok = __syncthreads_and(ma_ok);
+        for (int k = 0; k < 16; ++k) v[k] = e2[tid + LD2 * k];
+        dft<16, 1>(v);
+        float *orow = a.out + (size_t)z * (size_t)a.n + seg_out;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (vmask & (1u << j)) orow[j * NT + obase] = cabs2(v[j]);
     }
     if (!ok && tid == 0) {   // give outstanding copies and MMAs a bounded time to land
         atomicOr(a.status, STATUS_WAIT_TIMEOUT);
         if (!seg_ok) mbar_wait_bounded(&bar[0], 0, kWaitLimitNs);
-        if (h_iss0 > h_uses0) mbar_wait_bounded(&bar[1], h_uses0 & 1, kWaitLimitNs);
-        if (h_iss1 > h_uses1) mbar_wait_bounded(&bar[2], h_uses1 & 1, kWaitLimitNs);
-        if (b_done < b_uses) mbar_wait_bounded(&bar[3], (b_uses - 1) & 1, kWaitLimitNs);
-        if (a_done < a_uses) mbar_wait_bounded(&bar[4], (a_uses - 1) & 1, kWaitLimitNs);
+        if (h_iss > h_uses) mbar_wait_bounded(&bar[1], h_uses & 1, kWaitLimitNs);
+        if (b_done < b_uses) mbar_wait_bounded(&bar[2], (b_uses - 1) & 1, kWaitLimitNs);
     }
     fence_before_sync();
     __syncthreads();
@@ -345,6 +317,9 @@ cudaError_t launch_ols_tc(const CUtensorMap *tmap, const OlsArgs &a, const unsig
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !done[dev]) {
         e = cudaFuncSetAttribute(ols_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::Smem::total);
+        if (e == cudaSuccess)   // four blocks per SM need the largest shared-memory carveout
+            e = cudaFuncSetAttribute(ols_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) done[dev] = true;
     }
