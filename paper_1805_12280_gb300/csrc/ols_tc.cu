@@ -31,14 +31,13 @@ constexpr uint32_t A_LBO = 160, A_SBO = 640;            // padded: conflict-free
 constexpr uint32_t A_BYTES = 16 * A_SBO;                // 10240
 // B operand (the DFT matrix) [32 rows (n) x 32 fp16 (k)], K-major, no swizzle.
 constexpr uint32_t B_LBO = 128, B_SBO = 512, B_BYTES = 4 * B_SBO;   // 2048 per matrix
-constexpr uint32_t W_BYTES = 4 * B_BYTES;               // B' hi, B' lo, A' hi, A' lo
+constexpr uint32_t W_BYTES = 2 * B_BYTES;               // B' hi, B' lo
 constexpr uint32_t H_BYTES = sizeof(float2) * L;
 // TMEM columns: D of B' [0, 32), this thread's segment spectrum [32, 64), C' twiddles
 // [64, 96) and B' twiddles (times 16) [96, 128), kept there instead of registers.
 constexpr uint32_t TMEM_COLS = 128, COL_DB = 0, COL_X = 32, COL_TW1 = 64, COL_TW2 = 96;
 // kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
 constexpr uint32_t IDESC = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t WB_BYTES = 2 * B_BYTES;                // the B' matrices (hi, lo) in the block
 
 // 53.5 KB per block, so that four blocks share an SM: the segment buffer is the forward FFT's
 // first exchange and then the A operand of B'; one template buffer, refilled one ahead.
@@ -47,7 +46,7 @@ struct Smem {
     static constexpr size_t e2 = e1 + sizeof(float2) * L;            // exchange 2 (forward, A')
     static constexpr size_t hb = e2 + sizeof(float2) * 16 * LD2;     // template buffer
     static constexpr size_t wm = hb + H_BYTES;                       // B' hi, B' lo
-    static constexpr size_t bar = wm + WB_BYTES;                     // [0] segment+W, [1] template, [2] B' MMA
+    static constexpr size_t bar = wm + W_BYTES;                     // [0] segment+W, [1] template, [2] B' MMA
     static constexpr size_t slot = bar + 3 * 8;                      // TMEM address
     static constexpr size_t total = 128 + slot + 16;
     static_assert(sizeof(float2) * L >= A_BYTES, "A operand fits the segment buffer");
@@ -101,16 +100,17 @@ __device__ __forceinline__ void st_h2(unsigned char *base, uint32_t off, float r
     *reinterpret_cast<__half2 *>(base + off) = h;
 }
 
-// The four real 32 x 32 DFT matrices, written once per plan in the B-operand layout.
+// The real 32 x 32 inverse-DFT matrix of pass B' (times 1/16) as fp16 hi and lo parts,
+// written once per plan in the B-operand layout.
 __global__ void tc_matrix_kernel(unsigned char *out)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (matrix-pair p, n, k)
-    if (idx >= 2 * 32 * 32) return;
-    const int p = idx / 1024, n = (idx / 32) % 32, k = idx % 32;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (n, k)
+    if (idx >= 32 * 32) return;
+    const int n = idx / 32, k = idx % 32;
     const int b = n >> 1, ro = n & 1, kk = k >> 1, ri = k & 1;
     double s, c;
     sincospi(2.0 * (double)((kk * b) & 15) / 16.0, &s, &c);   // inverse 16-point DFT, exp(+2 pi i kk b / 16)
-    const double scale = p == 0 ? 1.0 / 16.0 : 16.0;         // B' pass, A' pass
+    const double scale = 1.0 / 16.0;
     // real form of (re_in + i im_in) * (c + i s): out_re = re c - im s, out_im = re s + im c
     double w;
     if (ro == 0) w = ri == 0 ? c : -s;
@@ -118,7 +118,7 @@ __global__ void tc_matrix_kernel(unsigned char *out)
     w *= scale;
     const __half hi = __double2half(w);
     const __half lo = __double2half(w - (double)__half2float(hi));
-    __half *base = reinterpret_cast<__half *>(out + (size_t)p * 2 * B_BYTES);
+    __half *base = reinterpret_cast<__half *>(out);
     base[b_off(n, k) / 2] = hi;
     base[(B_BYTES + b_off(n, k)) / 2] = lo;
 }
@@ -162,11 +162,11 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)) + WB_BYTES);
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(L * sizeof(float2)) + W_BYTES);
         const int c0 = seg * a.S - (a.K - 1);
 #pragma unroll
         for (int j = 0; j < L / 256; ++j) tma_load_1d(e1 + 256 * j, &tmap, c0 + 256 * j, &bar[0]);
-        bulk_load(wm, wmat, WB_BYTES, &bar[0]);
+        bulk_load(wm, wmat, W_BYTES, &bar[0]);
         if (z0 < z1) {
             mbar_arrive_expect_tx(&bar[1], H_BYTES);
             bulk_load(hb, a.H + (size_t)z0 * 8 * NT, H_BYTES, &bar[1]);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
 
 cudaError_t launch_tc_matrices(unsigned char *wmat, cudaStream_t s)
 {
-    tc::tc_matrix_kernel<<<(2 * 32 * 32 + 255) / 256, 256, 0, s>>>(wmat);
+    tc::tc_matrix_kernel<<<(32 * 32 + 255) / 256, 256, 0, s>>>(wmat);
     return cudaGetLastError();
 }
 
