@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -475,6 +476,13 @@ def bench_candidates(fd, h, dev, xd, x_host, reps=50, threshold=7.0):
         plan.status(stream)
         res["e2e"] = {"arrays_per_s": 1.0 / dt, "h2d_bytes": 8 * n, "d2h_bytes": 8 + 16 * ncand,
                       "api": "fdas_convolve_candidates with pinned host input and candidate list"}
+        # the secondary set: the power whose exponential tail has the one-sided Gaussian 6-sigma
+        # probability, T_g = -ln Q(6)
+        tg = -math.log(0.5 * math.erfc(6.0 / math.sqrt(2.0)))
+        ms_g = _events_ms(lambda: plan.candidates(xd, tg, buf.shape[0], stream, buf, cnt), reps, stream)
+        res["gaussian_tail_threshold"] = {"threshold": tg, "ms_per_array": ms_g,
+                                          "candidates_per_array": int(cnt.item())}
+        plan.status(stream)
     return res
 
 

@@ -6,11 +6,16 @@ threshold T = 7 (noise power is exponential with mean = sigma = 1 after the unit
 normalisation of inputs and templates).  Both sides must select the same points,
 except inside the band |P_ref - T| <= tol * max(P_ref), where rounding may decide.
 """
+import math
+
 import numpy as np
 
 TOL_FP32 = 1e-4
 TOL_TC = 2e-3
 THRESHOLD = 7.0
+# secondary set: the power whose exponential tail has the one-sided Gaussian 6-sigma
+# probability, -ln Q(6) = 20.74
+THRESHOLD_GAUSS = -math.log(0.5 * math.erfc(6.0 / math.sqrt(2.0)))
 
 
 def compare(p, p_ref, tol, threshold=THRESHOLD, scale=None):

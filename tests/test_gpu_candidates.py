@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity import THRESHOLD, TOL_FP32
+from parity import THRESHOLD, THRESHOLD_GAUSS, TOL_FP32
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +61,27 @@ def test_candidates_vs_oracle(fd, oracle_mod, bank):
     assert all(not sure[z, i] for z, i in extra)                   # the rest lie inside the band
     assert np.max(np.abs(got["power"] - ref[got["tpl"], got["bin"]])) <= band
     assert len(want) > 100
+
+
+def test_gaussian_tail_threshold_set(fd, oracle_mod, bank):
+    # the secondary set, T_g = -ln Q(6) = 20.74: at 2^17 points the chirp track crosses it
+    # (its peak grows with N: a^2 N / 2 = 164), the noise almost never does
+    x = synth.make_input(synth.single_small(n=1 << 17, seed=34))
+    with fd.Plan(bank, n_max=x.size) as plan:
+        xd = torch.from_numpy(x).cuda()
+        plane = plan.convolve(xd).cpu().numpy()
+        buf, count = plan.candidates(xd, threshold=THRESHOLD_GAUSS)
+        plan.status()
+        got = _keys(fd.candidates_to_numpy(buf, count))
+    zi, ii = np.nonzero(plane > THRESHOLD_GAUSS)
+    assert int(count.item()) == zi.size > 0
+    np.testing.assert_array_equal(got["tpl"], zi)
+    np.testing.assert_array_equal(got["bin"], ii)
+    ref = oracle_mod.direct_power(x, bank)
+    band = TOL_FP32 * ref.max()
+    sure = np.abs(ref - THRESHOLD_GAUSS) > band
+    assert np.array_equal((plane > THRESHOLD_GAUSS) & sure, (ref > THRESHOLD_GAUSS) & sure)
+    assert (ref > THRESHOLD_GAUSS).sum() < (ref > THRESHOLD).sum() / 10
 
 
 def test_candidate_overflow_and_empty(fd, bank):
