@@ -195,3 +195,25 @@ def test_bounded_wait_timeout_is_reported(fd, oracle_mod, bank):
         plan.status()                                    # read and cleared
         p = _run(fd, plan, x)
     compare(p, oracle_mod.direct_power(x, bank[:3]), TOL_FP32)
+
+
+@pytest.mark.slow
+def test_plane_beyond_2_31_elements(fd, oracle_mod, bank):
+    # 85 x (2^27 + 12345) plane = 45.6 GB: row offsets past 2^31 elements, a ragged last segment;
+    # sampled points (including the last rows and bins) against Eq. (1)
+    n = (1 << 27) + 12345
+    g = torch.Generator().manual_seed(61)
+    xc = torch.complex(torch.randn(n, generator=g), torch.randn(n, generator=g)).to(torch.complex64)
+    with fd.Plan(bank, n_max=n) as plan:
+        xd = xc.cuda()
+        out = plan.convolve(xd)
+        plan.status()
+        rng = np.random.default_rng(62)
+        zi = np.concatenate([rng.integers(0, 85, 1500), np.full(250, 84), np.full(250, 83)])
+        ii = np.concatenate([rng.integers(0, n, 1500), n - 1 - np.arange(250), rng.integers(n - 5000, n, 250)])
+        got = out[torch.from_numpy(zi).cuda(), torch.from_numpy(ii).cuda()].cpu().numpy()
+        scale = float(out.max().item())
+        del out, xd
+    torch.cuda.empty_cache()
+    ref = oracle_mod.direct_points(xc.numpy(), bank, zi, ii)
+    assert np.max(np.abs(got - ref)) <= TOL_FP32 * scale
