@@ -699,8 +699,11 @@ def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=3
     return res
 
 
-KERNEL_SOURCES = {"fp32": ("ols_fp32.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "fdas_internal.cuh"),
-                  "tc": ("ols_tc.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "fdas_internal.cuh")}
+# the sources a segment kernel is compiled from, and the plan kernel that lays out the templates it reads
+KERNEL_SOURCES = {"fp32": ("ols_fp32.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "tmem.cuh", "fdas_internal.cuh",
+                           "plan_kernels.cu"),
+                  "tc": ("ols_tc.cu", "ols_common.cuh", "fft_regs.cuh", "fft_split.cuh", "ptx.cuh", "tmem.cuh",
+                         "fdas_internal.cuh", "plan_kernels.cu")}
 
 
 def _code_only(text: str) -> str:

@@ -324,7 +324,8 @@ int build_templates(fdas_plan p, const float2 *d_h32, int L)
     if ((e = cudaMalloc(&p->d_H, sizeof(float4) * (size_t)p->M * 8 * (L / 16))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc templates");
     if ((e = fdas::launch_twiddles(L, p->d_tw64, p->d_tw, nullptr)) != cudaSuccess) return cuda_fail(e, "twiddle kernel");
-    if ((e = fdas::launch_pretransform(L, d_h32, p->M, p->K_user, p->d_tw64, p->d_H, nullptr)) != cudaSuccess)
+    if ((e = fdas::launch_pretransform(L, d_h32, p->M, p->K_user, p->d_tw64, p->d_H,
+                                        p->precision == FDAS_PREC_TC_FP16, nullptr)) != cudaSuccess)
         return cuda_fail(e, "pretransform kernel");
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan-time kernels");
     p->L = L;

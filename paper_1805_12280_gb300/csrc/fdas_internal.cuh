@@ -140,7 +140,9 @@ cudaError_t fdfir_forward(int P2, const float2 *in, int64_t len, const float2 *t
                           float scale, cudaStream_t s);
 cudaError_t fdfir_inverse(int P2, const float2 *X, const float2 *H, float2 *B, const float2 *tw1, const float2 *tw2,
                           float *out, int64_t n, cudaStream_t s);
+// split: the slot pairs (c, 8 + c) as (re_c, re_{8+c}, im_c, im_{8+c}) (tensor-core form),
+// else the slot pairs (2p, 2p + 1) as two complex values.
 cudaError_t launch_pretransform(int L, const float2 *h32, int M, int K, const double2 *w64,
-                                float4 *Hperm, cudaStream_t s);
+                                float4 *Hperm, bool split, cudaStream_t s);
 
 }  // namespace fdas

@@ -16,6 +16,7 @@
 
 #include "fdas_internal.cuh"
 #include "fft_regs.cuh"
+#include "fft_split.cuh"
 #include "ols_common.cuh"
 #include "ptx.cuh"
 #include "tmem.cuh"
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
 #pragma unroll
             for (int c = 0; c < R; ++c) tw[g * R + c] = cconj(__ldg(&a.tw[(16 * c * k2) & MASK]));
         }
-        tmem_st_c16(my + COL_TW1, tw);
+        tmem_st_split16(my + COL_TW1, tw);   // split pairs (c, R + c)
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             const float2 w = __ldg(&a.tw[((b * R + hi) * k1) & MASK]);
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
     if (ok) {
         float2 X[16];
         forward_fft<L>(e1, e2, a.tw, v, X);
-        tmem_st_c16(my + COL_X, X);   // the spectrum waits in TMEM for the template loop
+        tmem_st_split16(my + COL_X, X);   // the spectrum waits in TMEM (split pairs) for the template loop
         __syncthreads();              // e1 is read: it becomes the A operand of B'
     }
     const int64_t seg_out = (int64_t)seg * a.S;
@@ -215,26 +216,32 @@ __global__ void __launch_bounds__(128, FDAS_TC_MINB)
         const bool h_ok = mbar_wait_bounded(&bar[1], h_uses & 1, kWaitLimitNs);
         h_uses++;
         // ---- product with H_z, pass C' (radix 8), twiddle, fp16 rows of the B' operand
-        tmem_ld_c16(my + COL_X, v);
-#pragma unroll
-        for (int jp = 0; jp < 8; ++jp) {
-            const float4 h = hb[jp * NT + tid];
-            v[2 * jp] = cmul(v[2 * jp], make_float2(h.x, h.y));
-            v[2 * jp + 1] = cmul(v[2 * jp + 1], make_float2(h.z, h.w));
-        }
-        dft<R, 1, 1, 0>(v);
-        dft<R, 1, 1, R>(v);
+        // (both pass-C' groups as split pairs: packed FP32x2 product, DFTs and twiddles)
         {
-            float2 tw1[16];
-            tmem_ld_c16(my + COL_TW1, tw1);
+            float2 re[8], im[8];
+            {
+                uint32_t xr[32];
+                tmem_ld32(my + COL_X, xr);
+                split_from_cols(xr, re, im);
+            }
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                const int k2 = hi + 8 * g;
+            for (int c = 0; c < 8; ++c) {
+                const float4 h = hb[c * NT + tid];
+                cmul_split(re[c], im[c], make_float2(h.x, h.y), make_float2(h.z, h.w));
+            }
+            dft8x2_split<1>(re, im);
+            {
+                uint32_t t1r[32];
+                tmem_ld32(my + COL_TW1, t1r);
+                float2 twr[8], twi[8];
+                split_from_cols(t1r, twr, twi);
 #pragma unroll
-                for (int c = 0; c < R; ++c) {
-                    const float2 y = (c == 0) ? v[g * R] : cmul(v[g * R + c], tw1[g * R + c]);
-                    st_h2(aB, a_off(k1 + 16 * c, 2 * k2), y.x, y.y);   // row (k1, c), K pair k2
-                }
+                for (int c = 1; c < 8; ++c) cmul_split(re[c], im[c], twr[c], twi[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < R; ++c) {   // row (k1, c), K pairs k2 = hi and hi + 8
+                st_h2(aB, a_off(k1 + 16 * c, 2 * hi), re[c].x, im[c].x);
+                st_h2(aB, a_off(k1 + 16 * c, 2 * (hi + 8)), re[c].y, im[c].y);
             }
         }
         fence_proxy_async_smem();

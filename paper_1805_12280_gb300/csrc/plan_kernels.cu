@@ -25,7 +25,7 @@ __global__ void twiddle_kernel(int L, double2 *w64, float2 *w32)
 
 // One thread per (template z, thread slot tau, register slot j).
 __global__ void pretransform_kernel(int L, const float2 *__restrict__ h32, int M, int K,
-                                    const double2 *__restrict__ w64, float4 *__restrict__ Hperm)
+                                    const double2 *__restrict__ w64, float4 *__restrict__ Hperm, bool split)
 {
     const int NT = L / 16;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,9 +45,15 @@ __global__ void pretransform_kernel(int L, const float2 *__restrict__ h32, int M
     }
     re /= (double)L;
     im /= (double)L;
-    float *dst = reinterpret_cast<float *>(Hperm + ((size_t)z * 8 + j / 2) * NT + tau) + 2 * (j & 1);
-    dst[0] = (float)re;
-    dst[1] = (float)im;
+    if (!split) {   // slots (2p, 2p+1) as two complex values
+        float *dst = reinterpret_cast<float *>(Hperm + ((size_t)z * 8 + j / 2) * NT + tau) + 2 * (j & 1);
+        dst[0] = (float)re;
+        dst[1] = (float)im;
+    } else {        // slots (c, 8 + c) as split pairs (re_c, re_{8+c}, im_c, im_{8+c})
+        float *dst = reinterpret_cast<float *>(Hperm + ((size_t)z * 8 + (j & 7)) * NT + tau);
+        dst[j >> 3] = (float)re;
+        dst[2 + (j >> 3)] = (float)im;
+    }
 }
 
 cudaError_t launch_twiddles(int L, double2 *w64, float2 *w32, cudaStream_t s)
@@ -57,10 +63,10 @@ cudaError_t launch_twiddles(int L, double2 *w64, float2 *w32, cudaStream_t s)
 }
 
 cudaError_t launch_pretransform(int L, const float2 *h32, int M, int K, const double2 *w64, float4 *Hperm,
-                                cudaStream_t s)
+                                bool split, cudaStream_t s)
 {
     const int64_t total = (int64_t)M * (L / 16) * 16;
-    pretransform_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L, h32, M, K, w64, Hperm);
+    pretransform_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L, h32, M, K, w64, Hperm, split);
     return cudaGetLastError();
 }
 
