@@ -355,6 +355,7 @@ def run_fdas(args):
         del out
         torch.cuda.empty_cache()
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
+                 "harmonic_sum": bench_harmonic(fd, h, dev, xd),
                  "template_groups": bench_groups(fd, h, dev, xd),
                  "library_unfused_ols": bench_library_ols(h, dev, xd),
                  "full_fdfir": bench_fdfir(fd, h, dev, xd),
@@ -482,6 +483,45 @@ def bench_candidates(fd, h, dev, xd, x_host, reps=50, threshold=7.0):
         ms_g = _events_ms(lambda: plan.candidates(xd, tg, buf.shape[0], stream, buf, cnt), reps, stream)
         res["gaussian_tail_threshold"] = {"threshold": tg, "ms_per_array": ms_g,
                                           "candidates_per_array": int(cnt.item())}
+        plan.status(stream)
+    return res
+
+
+def bench_harmonic(fd, h, dev, xd, reps=20):
+    """Harmonic summing (fdas_harmonic_sum) of the headline array's plane: sums of 8 and 16
+    harmonics at bin k r, drift k z, thresholds h + 6 sqrt(h); and the chain plane + sums."""
+    import torch
+    n, m = xd.numel(), h.shape[0]
+    bin0 = (h.shape[1] - 1) // 2
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = measured_peaks()
+    # every cell the sums read at least once: the plane from column bin0 + 1 on
+    plane_bytes = 4 * m * (n - 1 - bin0)
+    res = {"workload": f"plane of the N=2^22, 85-template array (1.43 GB, larger than L2), bin0={bin0}",
+           "algorithmic_bytes": plane_bytes}
+    with fd.Plan(h, n_max=n) as plan:
+        plane = plan.convolve(xd)
+        buf = torch.empty((1 << 21, 3), dtype=torch.int64, device=dev)
+        cnt = torch.empty(1, dtype=torch.int64, device=dev)
+        for H in (8, 16):
+            thr = fd.harmonic_thresholds(H)
+            run = lambda: fd.harmonic_sum(plane, bin0, H, thr, buf.shape[0], stream, buf, cnt)   # noqa: E731
+            for _ in range(3):
+                run()
+            ms = _events_ms(run, reps, stream)
+            res[f"max_harm_{H}"] = {"ms_per_array": ms, "candidates": int(cnt.item()),
+                                    "plane_read_gbs": plane_bytes / (ms / 1e3) / 1e9,
+                                    "hbm_frac": plane_bytes / (ms / 1e3) / 1e9 / peak,
+                                    "thresholds": [round(t, 3) for t in thr]}
+
+        def chain():
+            plan.convolve(xd, plane, stream)
+            fd.harmonic_sum(plane, bin0, 8, fd.harmonic_thresholds(8), buf.shape[0], stream, buf, cnt)
+        for _ in range(3):
+            chain()
+        ms = _events_ms(chain, reps, stream)
+        res["plane_then_sums_8"] = {"ms_per_array": ms, "arrays_per_s": 1e3 / ms}
+        res["peak_kind"] = peak_kind
         plan.status(stream)
     return res
 

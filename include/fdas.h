@@ -271,6 +271,45 @@ int fdas_fdfir_convolve(fdas_fdfir f, const void *in_c64_dev, int64_t n, float *
 int fdas_fdfir_destroy(fdas_fdfir f);
 
 /* ------------------------------------------------------------------------------------
+ * Harmonic summing of a power plane (the module that receives the plane, Sec. 3; the
+ * paper names it without defining it, read here as the incoherent harmonic sum).
+ *
+ * Rows are ordered by drift: row y holds drift z = y - c, c = (n_templates - 1) / 2 (the
+ * order of the bank z = -c .. c); column bin0 holds frequency bin 0 (templates centred in a
+ * frame of F taps delay the plane by (F - 1) / 2 bins: bin0 = 210 for 421-tap frames).  The
+ * k-th harmonic of a signal at bin r with drift z lies at bin k r with drift k z, so for the
+ * fundamental (r, z), r >= 1,
+ *     S_h(r, z) = sum_{k=1..h} P[c + k z][bin0 + k r]     (FP32, added for k = 1, 2, ..)
+ * for h = 1, 2, 4, .., max_harm, defined where |h z| <= c and bin0 + h r <= n - 1.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t tpl;       /* row of the fundamental, c + z */
+    float   power;     /* S_h */
+    int64_t bin;       /* column of the fundamental, bin0 + r */
+    int32_t nharm;     /* h */
+    int32_t reserved;  /* 0 */
+} fdas_harmonic_candidate;
+
+/*
+ * fdas_harmonic_sum -- every defined S_h(r, z) > thresholds[log2 h] is appended to cand_dev.
+ *
+ *   plane_dev   : device float32 [n_templates][n], row-major, 4-byte aligned (the plane
+ *                 fdas_convolve writes); n_templates odd; n >= 1; 0 <= bin0 < n.
+ *   max_harm    : 1, 2, 4, 8, 16 or 32.
+ *   thresholds  : host float [log2(max_harm) + 1], one per level h = 1, 2, .., max_harm.
+ *   cand_dev    : device array of max_cand records (8-byte aligned; may be null if
+ *                 max_cand = 0).
+ *   count_dev   : device unsigned 64-bit counter (8-byte aligned), cleared on `stream`
+ *                 before the launch; afterwards the number of crossings, which may exceed
+ *                 max_cand (then only max_cand were stored).
+ * Runs on the current device; the order of the records is unspecified.  Asynchronous
+ * (one memset and at most one kernel launch on `stream`).  Errors: INVALID_ARG, CUDA.
+ */
+int fdas_harmonic_sum(const float *plane_dev, int n_templates, int64_t n, int64_t bin0, int max_harm,
+                      const float *thresholds, fdas_harmonic_candidate *cand_dev, int64_t max_cand,
+                      unsigned long long *count_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------
  * Served form: continuous batching over one plan.
  *
  * Requests (device input arrays) are admitted in arrival order as soon as the memory

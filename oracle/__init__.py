@@ -9,6 +9,9 @@ Functions (each restates the paper, see ``fdas_oracle.c``):
   direct_conv   Eq. (1), complex output          direct_power   Eq. (1) + |y|^2
   direct_points Eq. (1) + |y|^2 at chosen points fft            unnormalised radix-2 DFT
   ols_power     Algorithm 2 (overlap-save) + |y|^2
+  harmonic_sums / harmonic_candidates
+                the harmonic-summing stage on the power plane (Sec. 3 names it;
+                read as the incoherent sum of the powers at bin k r, drift k z)
 """
 from __future__ import annotations
 
@@ -56,6 +59,10 @@ def _load():
             lib.oracle_fft.restype = ci
             lib.oracle_ols_power.argtypes = [P, i64, P, ci, ci, ci, ci, P]
             lib.oracle_ols_power.restype = ci
+            lib.oracle_harmonic_sums.argtypes = [P, ci, i64, i64, ci, P]
+            lib.oracle_harmonic_sums.restype = ci
+            lib.oracle_harmonic_candidates.argtypes = [P, ci, i64, i64, ci, P, P, P, P, P, i64]
+            lib.oracle_harmonic_candidates.restype = i64
             _lib = lib
     return _lib
 
@@ -135,3 +142,49 @@ def ols_power(x, h, L: int = 2048, S: int | None = None) -> np.ndarray:
     if _load().oracle_ols_power(_ptr(x), x.size, _ptr(h), m, k, int(L), int(S), _ptr(p)) != 0:
         raise ValueError(f"invalid overlap-save arguments (n={x.size}, K={k}, L={L}, S={S})")
     return p
+
+
+def _plane32(P) -> np.ndarray:
+    P = np.ascontiguousarray(P, dtype=np.float32)
+    if P.ndim != 2:
+        raise ValueError("the plane must be 2-D [m, n]")
+    return P
+
+
+def harmonic_levels(max_harm: int) -> list[int]:
+    """The harmonic counts h = 1, 2, 4, .., max_harm summed."""
+    return [1 << j for j in range(int(max_harm).bit_length())]
+
+
+def harmonic_sums(P, bin0: int, max_harm: int) -> np.ndarray:
+    """S_h(r, z) = sum_{k<=h} P[c + k z][bin0 + k r] for h = 1, 2, .., max_harm, float64
+    [nlev, m, n] at (level, c + z, bin0 + r); NaN where undefined (r < 1, |h z| > c or
+    bin0 + h r > n - 1).  P: float32 [m, n], m odd, c = (m - 1) / 2."""
+    P = _plane32(P)
+    m, n = P.shape
+    S = np.empty((len(harmonic_levels(max_harm)), m, n), dtype=np.float64)
+    if _load().oracle_harmonic_sums(_ptr(P), m, n, int(bin0), int(max_harm), _ptr(S)) != 0:
+        raise ValueError(f"invalid harmonic-sum arguments (m={m}, n={n}, bin0={bin0}, max_harm={max_harm})")
+    return S
+
+
+def harmonic_candidates(P, bin0: int, max_harm: int, thresholds) -> dict:
+    """Crossings S_h > thresholds[j] (h = 2^j) in (level, row, bin) order: a dict of arrays
+    ``level`` (j), ``row`` (c + z), ``bin`` (bin0 + r) and ``value`` (S_h, float64)."""
+    P = _plane32(P)
+    m, n = P.shape
+    nlev = len(harmonic_levels(max_harm))
+    thr = np.ascontiguousarray(thresholds, dtype=np.float64)
+    if thr.shape != (nlev,):
+        raise ValueError(f"need {nlev} thresholds")
+    lib = _load()
+    empty = [np.empty(0, dtype=t) for t in (np.int32, np.int32, np.int64, np.float64)]
+    total = lib.oracle_harmonic_candidates(_ptr(P), m, n, int(bin0), int(max_harm), _ptr(thr),
+                                           *[_ptr(a) for a in empty], 0)
+    if total < 0:
+        raise ValueError(f"invalid harmonic-sum arguments (m={m}, n={n}, bin0={bin0}, max_harm={max_harm})")
+    out = [np.empty(total, dtype=t) for t in (np.int32, np.int32, np.int64, np.float64)]
+    got = lib.oracle_harmonic_candidates(_ptr(P), m, n, int(bin0), int(max_harm), _ptr(thr),
+                                         *[_ptr(a) for a in out], total)
+    assert got == total
+    return dict(zip(("level", "row", "bin", "value"), out))

@@ -21,8 +21,16 @@
  *       is preceded by K-1 zeros): FFT, element-wise product, inverse FFT,
  *       discard the first K-1 points, concatenate; then |y|^2.
  *
+ *   oracle_harmonic_sums / oracle_harmonic_candidates
+ *       the harmonic-summing stage that receives the power plane (Sec. 3 names
+ *       it without defining it; read as the incoherent harmonic sum): for the
+ *       fundamental at frequency bin r >= 1 and drift z, the powers at bin k r,
+ *       drift k z, k = 1..h, added for h = 1, 2, 4, .., max_harm.
+ *
  * Parity: pinned by tests against brute force (numpy.convolve), a delta
- * template, linearity, Parseval, numpy's FFT and the direct form.
+ * template, linearity, Parseval, numpy's FFT and the direct form; the harmonic
+ * sums against closed forms (planes linear in row and column, constant planes,
+ * single cells, injected harmonic trains).
  */
 #include <math.h>
 #include <stdint.h>
@@ -201,4 +209,109 @@ int oracle_ols_power(const double *x, int64_t n, const double *h, int m, int k_l
     }
     free(H);
     return fail ? -1 : 0;
+}
+
+/*
+ * Harmonic sums of a power plane P [m][n] (float32, as stored), m odd, rows
+ * ordered by drift z = y - c with c = (m-1)/2, column bin0 holding frequency
+ * bin 0.  For the fundamental (r, z), r >= 1:
+ *     S_h(r, z) = sum_{k=1..h} P[c + k z][bin0 + k r]        (added for k = 1, 2, ..)
+ * defined where |h z| <= c and bin0 + h r <= n - 1, for the levels
+ * h = 2^j <= max_harm.  S is [nlev][m][n] in FP64, cell (j, c + z, bin0 + r);
+ * NaN where S_h is undefined.  Returns 0, or -1 on invalid arguments.
+ */
+static int harmonic_args_ok(int m, int64_t n, int64_t bin0, int max_harm)
+{
+    if (m < 1 || (m & 1) == 0 || n < 1 || bin0 < 0 || bin0 >= n) return 0;
+    if (max_harm < 1 || max_harm > 32 || (max_harm & (max_harm - 1))) return 0;
+    return 1;
+}
+
+static int harmonic_levels(int max_harm)
+{
+    int nlev = 0;
+    while ((1 << nlev) <= max_harm) ++nlev;
+    return nlev;
+}
+
+int oracle_harmonic_sums(const float *P, int m, int64_t n, int64_t bin0, int max_harm, double *S)
+{
+    if (!harmonic_args_ok(m, n, bin0, max_harm)) return -1;
+    const int c = (m - 1) / 2, nlev = harmonic_levels(max_harm);
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < m; ++y) {
+        const int z = y - c;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t r = i - bin0;
+            double acc = 0.0;
+            int k = 1;
+            for (int j = 0; j < nlev; ++j) {
+                const int h = 1 << j;
+                int defined = r >= 1 && (int64_t)h * (z < 0 ? -z : z) <= c && bin0 + (int64_t)h * r <= n - 1;
+                if (defined) {
+                    for (; k <= h; ++k) acc += (double)P[(int64_t)(c + k * z) * n + bin0 + k * r];
+                }
+                S[((int64_t)j * m + y) * n + i] = defined ? acc : NAN;
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * The crossings S_h(r, z) > thr[j] (h = 2^j) of the same sums, in the order
+ * (j, y, i) ascending: level j, row y = c + z, column i = bin0 + r and the sum.
+ * Stores at most cap of them; returns their total count, or -1 on invalid
+ * arguments or allocation failure.
+ */
+int64_t oracle_harmonic_candidates(const float *P, int m, int64_t n, int64_t bin0, int max_harm,
+                                   const double *thr, int32_t *lev_out, int32_t *row_out,
+                                   int64_t *bin_out, double *val_out, int64_t cap)
+{
+    if (!harmonic_args_ok(m, n, bin0, max_harm)) return -1;
+    const int c = (m - 1) / 2, nlev = harmonic_levels(max_harm);
+    int64_t *cnt = (int64_t *)calloc((size_t)nlev * m + 1, sizeof(int64_t));
+    if (!cnt) return -1;
+    for (int pass = 0; pass < 2; ++pass) {
+        /* pass 0 counts the crossings of each (level, row); pass 1 stores them */
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int y = 0; y < m; ++y) {
+            const int z = y - c;
+            int64_t next[32];
+            for (int j = 0; j < nlev; ++j) next[j] = pass ? cnt[(int64_t)j * m + y] : 0;
+            for (int64_t i = bin0 + 1; i < n; ++i) {
+                const int64_t r = i - bin0;
+                double acc = 0.0;
+                int k = 1;
+                for (int j = 0; j < nlev; ++j) {
+                    const int h = 1 << j;
+                    if ((int64_t)h * (z < 0 ? -z : z) > c || bin0 + (int64_t)h * r > n - 1) break;
+                    for (; k <= h; ++k) acc += (double)P[(int64_t)(c + k * z) * n + bin0 + k * r];
+                    if (acc > thr[j]) {
+                        const int64_t at = next[j]++;
+                        if (pass && at < cap) {
+                            lev_out[at] = j;
+                            row_out[at] = y;
+                            bin_out[at] = i;
+                            val_out[at] = acc;
+                        }
+                    }
+                }
+            }
+            if (!pass)
+                for (int j = 0; j < nlev; ++j) cnt[(int64_t)j * m + y] = next[j];
+        }
+        if (!pass) {   /* exclusive prefix over (level, row) */
+            int64_t run = 0;
+            for (int64_t q = 0; q < (int64_t)nlev * m; ++q) {
+                const int64_t v = cnt[q];
+                cnt[q] = run;
+                run += v;
+            }
+            cnt[(int64_t)nlev * m] = run;
+        }
+    }
+    const int64_t total = cnt[(int64_t)nlev * m];
+    free(cnt);
+    return total;
 }

@@ -1,0 +1,169 @@
+// Harmonic summing of a power plane: the stage that receives the plane from the
+// FT-convolution module (Sec. 3 names it; read here as the incoherent harmonic sum).
+//
+// Rows of the plane are ordered by drift, z = y - c with c = (m-1)/2, and column bin0
+// holds frequency bin 0 (for templates centred in a frame of F taps, bin0 = (F-1)/2).
+// The k-th harmonic of a signal at bin r with drift z lies at bin k r with drift k z, so for
+// the fundamental (r, z), r >= 1,
+//     S_h(r, z) = sum_{k=1..h} P[c + k z][bin0 + k r],      h = 1, 2, 4, .., H,
+// is defined where |h z| <= c and bin0 + h r <= n - 1, and every S_h above its level's
+// threshold becomes a candidate.
+//
+// One thread per fundamental: the H loads of its harmonics are issued together (predicated
+// on the harmonic lying inside the plane), then added in the order k = 1, 2, .., the running
+// sum compared with the threshold at every power of two.  A block takes tiles of 2048
+// consecutive fundamentals of one row (the k = 1 loads of a warp are one 128-byte line; the
+// k-th are a k-strided gather, served by L2 for the neighbouring warps of the tile); its
+// crossings are staged in shared memory and reserved in the output with one atomic per tile.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "fdas_internal.cuh"
+
+namespace fdas {
+namespace {
+
+constexpr int kHsThreads = 256;
+constexpr int kHsPerThread = 8;                      // fundamentals per thread and tile
+constexpr int64_t kHsTile = kHsThreads * kHsPerThread;
+constexpr int kHsStage = 256;                        // records staged per block and tile
+constexpr int kHsMaxLevels = 6;                      // h = 1 .. 32
+
+struct HsThresholds {
+    float t[kHsMaxLevels];
+};
+
+template <int H>
+__global__ void __launch_bounds__(kHsThreads) harmonic_kernel(const float *__restrict__ P, int m, int64_t n,
+                                                              int64_t bin0, int64_t tiles_per_row, HsThresholds thr,
+                                                              fdas_harmonic_candidate *__restrict__ out,
+                                                              int64_t max_cand, unsigned long long *__restrict__ count)
+{
+    __shared__ fdas_harmonic_candidate stage[kHsStage];
+    __shared__ unsigned n_staged, n_flush;
+    __shared__ unsigned long long flush_base;
+    const int c = (m - 1) / 2;
+    const int64_t rmax = n - 1 - bin0;   // fundamentals r = 1 .. rmax
+    const int64_t tiles = (int64_t)m * tiles_per_row;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int y = (int)(tile / tiles_per_row);
+        const int z = y - c;
+        const int az = z < 0 ? -z : z;
+        const int kz = az == 0 ? H : min(H, c / az);   // harmonics whose drift k z lies in the plane
+        const int64_t r0 = 1 + (tile - (int64_t)y * tiles_per_row) * kHsTile;
+        const int64_t origin = (int64_t)c * n + bin0;   // cell of k = 0
+        const int64_t step_z = (int64_t)z * n;
+        if (threadIdx.x == 0) n_staged = 0;
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < kHsPerThread; ++q) {
+            const int64_t r = r0 + q * kHsThreads + threadIdx.x;
+            if (r > rmax) break;
+            const int64_t step = step_z + r;   // from harmonic k to k + 1
+            float v[H];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const bool in = k <= kz && (int64_t)k * r <= rmax;
+                v[k - 1] = in ? __ldg(P + origin + (int64_t)k * step) : 0.f;
+            }
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                acc += v[k - 1];
+                if ((k & (k - 1)) == 0) {   // level h = k
+                    const int j = 31 - __clz(k);
+                    if (k <= kz && (int64_t)k * r <= rmax && acc > thr.t[j]) {
+                        fdas_harmonic_candidate rec;
+                        rec.tpl = y;
+                        rec.power = acc;
+                        rec.bin = bin0 + r;
+                        rec.nharm = k;
+                        rec.reserved = 0;
+                        const unsigned slot = atomicAdd(&n_staged, 1u);
+                        if (slot < (unsigned)kHsStage) {
+                            stage[slot] = rec;
+                        } else {   // staging full: reserve this record on its own
+                            const unsigned long long at = atomicAdd(count, 1ull);
+                            if ((long long)at < max_cand) out[at] = rec;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned ns = min(n_staged, (unsigned)kHsStage);
+            n_flush = ns;
+            flush_base = ns ? atomicAdd(count, (unsigned long long)ns) : 0ull;
+        }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < n_flush; i += kHsThreads)
+            if ((long long)(flush_base + i) < max_cand) out[flush_base + i] = stage[i];
+        __syncthreads();   // the stage is read before the next tile refills it
+    }
+}
+
+template <int H>
+cudaError_t launch_h(const float *P, int m, int64_t n, int64_t bin0, const HsThresholds &thr,
+                     fdas_harmonic_candidate *out, int64_t max_cand, unsigned long long *count, cudaStream_t s)
+{
+    const int64_t rmax = n - 1 - bin0;
+    const int64_t tiles_per_row = (rmax + kHsTile - 1) / kHsTile;
+    const int64_t tiles = (int64_t)m * tiles_per_row;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harmonic_kernel<H>, kHsThreads, 0)) != cudaSuccess)
+        return e;
+    const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(tiles < resident ? tiles : resident);
+    harmonic_kernel<H><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count);
+    return cudaGetLastError();
+}
+
+int hs_cuda(cudaError_t e, const char *what)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return set_error(FDAS_ERR_CUDA, buf);
+}
+
+}  // namespace
+}  // namespace fdas
+
+extern "C" int fdas_harmonic_sum(const float *plane_dev, int n_templates, int64_t n, int64_t bin0, int max_harm,
+                                 const float *thresholds, fdas_harmonic_candidate *cand_dev, int64_t max_cand,
+                                 unsigned long long *count_dev, void *stream)
+{
+    using namespace fdas;
+    if (!plane_dev || !count_dev || !thresholds || (max_cand > 0 && !cand_dev))
+        return set_error(FDAS_ERR_INVALID_ARG, "null pointer");
+    if (max_cand < 0) return set_error(FDAS_ERR_INVALID_ARG, "max_cand must be >= 0");
+    if (n_templates < 1 || (n_templates & 1) == 0)
+        return set_error(FDAS_ERR_INVALID_ARG, "n_templates must be odd (rows z = -c .. c)");
+    if (n < 1 || bin0 < 0 || bin0 >= n) return set_error(FDAS_ERR_INVALID_ARG, "need n >= 1 and 0 <= bin0 < n");
+    if (max_harm < 1 || max_harm > 32 || (max_harm & (max_harm - 1)))
+        return set_error(FDAS_ERR_INVALID_ARG, "max_harm must be a power of two in [1, 32]");
+    if (reinterpret_cast<uintptr_t>(plane_dev) % 4 || reinterpret_cast<uintptr_t>(count_dev) % 8 ||
+        reinterpret_cast<uintptr_t>(cand_dev) % 8)
+        return set_error(FDAS_ERR_INVALID_ARG, "misaligned plane, counter or candidate array");
+    HsThresholds thr{};
+    for (int j = 0; (1 << j) <= max_harm; ++j) thr.t[j] = thresholds[j];
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return hs_cuda(e, "clear candidate counter");
+    if (n - 1 - bin0 < 1) return FDAS_OK;   // no fundamental r >= 1 inside the plane
+    switch (max_harm) {
+    case 1: e = launch_h<1>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
+    case 2: e = launch_h<2>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
+    case 4: e = launch_h<4>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
+    case 8: e = launch_h<8>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
+    case 16: e = launch_h<16>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
+    default: e = launch_h<32>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
+    }
+    if (e != cudaSuccess) return hs_cuda(e, "harmonic-sum launch");
+    return FDAS_OK;
+}

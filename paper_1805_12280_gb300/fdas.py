@@ -54,6 +54,15 @@ class fdas_candidate(ctypes.Structure):
 CANDIDATE_DTYPE = np.dtype([("tpl", "<i4"), ("power", "<f4"), ("bin", "<i8")])
 
 
+class fdas_harmonic_candidate(ctypes.Structure):
+    _fields_ = [("tpl", ctypes.c_int32), ("power", ctypes.c_float), ("bin", ctypes.c_int64),
+                ("nharm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+HARMONIC_DTYPE = np.dtype([("tpl", "<i4"), ("power", "<f4"), ("bin", "<i8"), ("nharm", "<i4"),
+                           ("reserved", "<i4")])
+
+
 class fdas_server_opts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("lanes", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
@@ -98,6 +107,7 @@ SIGNATURES = {
     "fdas_fdfir_length": (_I, [_P, ctypes.POINTER(_I64)]),
     "fdas_fdfir_convolve": (_I, [_P, _P, _I64, _P, _P]),
     "fdas_fdfir_destroy": (_I, [_P]),
+    "fdas_harmonic_sum": (_I, [_P, _I, _I64, _I64, _I, ctypes.POINTER(ctypes.c_float), _P, _I64, _P, _P]),
     "fdas_strerror": (ctypes.c_char_p, [_I]),
     "fdas_last_error": (ctypes.c_char_p, []),
     "fdas_version": (ctypes.c_char_p, []),
@@ -273,6 +283,57 @@ def fdas_fdfir_destroy(plan: int) -> None:
 
 
 # ---- convenience wrapper for torch tensors ---------------------------------
+
+def fdas_harmonic_sum(plane_ptr: int, n_templates: int, n: int, bin0: int, max_harm: int, thresholds,
+                      cand_ptr: int, max_cand: int, count_ptr: int, stream: int = 0) -> None:
+    thr = (ctypes.c_float * len(thresholds))(*[float(t) for t in thresholds])
+    _check(load().fdas_harmonic_sum(_P(plane_ptr), int(n_templates), int(n), int(bin0), int(max_harm), thr,
+                                    _P(cand_ptr), int(max_cand), _P(count_ptr), _P(stream)), "fdas_harmonic_sum")
+
+
+def harmonic_levels(max_harm: int) -> list:
+    """The harmonic counts h = 1, 2, 4, .., max_harm whose sums are thresholded."""
+    return [1 << j for j in range(int(max_harm).bit_length())]
+
+
+def harmonic_thresholds(max_harm: int, sigmas: float = 6.0) -> list:
+    """mu + sigmas * sd of a sum of h unit-exponential noise powers (mean h, sd sqrt(h)) for
+    each level: at h = 1 this is the single-plane threshold 1 + 6 = 7."""
+    return [h + sigmas * float(np.sqrt(h)) for h in harmonic_levels(max_harm)]
+
+
+def harmonic_sum(plane, bin0: int, max_harm: int = 8, thresholds=None, max_cand: int = 1 << 20, stream=None,
+                 buf=None, count=None):
+    """Harmonic-sum crossings of a device float32 plane [n_templates, n] (rows z = -c .. c).
+
+    Returns (buf, count): ``buf`` a device int64 tensor [max_cand, 3] holding
+    fdas_harmonic_candidate records, ``count`` a device int64 tensor [1] with the number of
+    crossings; ``harmonic_to_numpy`` decodes them.  ``thresholds`` defaults to
+    ``harmonic_thresholds(max_harm)``.
+    """
+    import torch
+    if plane.dtype != torch.float32 or not plane.is_cuda or not plane.is_contiguous() or plane.dim() != 2:
+        raise ValueError("plane must be a contiguous 2-D float32 CUDA tensor")
+    if thresholds is None:
+        thresholds = harmonic_thresholds(max_harm)
+    if len(thresholds) != len(harmonic_levels(max_harm)):
+        raise ValueError(f"need {len(harmonic_levels(max_harm))} thresholds for max_harm={max_harm}")
+    if buf is None:
+        buf = torch.empty((max(max_cand, 1), 3), dtype=torch.int64, device=plane.device)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=plane.device)
+    with torch.cuda.device(plane.device):
+        fdas_harmonic_sum(plane.data_ptr(), plane.shape[0], plane.shape[1], bin0, max_harm, thresholds,
+                          buf.data_ptr(), min(max_cand, buf.shape[0]), count.data_ptr(), _stream_handle(stream))
+    return buf, count
+
+
+def harmonic_to_numpy(buf, count) -> np.ndarray:
+    """Host copy of the stored harmonic-sum records as a structured array."""
+    n = int(count.item()) if hasattr(count, "item") else int(count)
+    n = min(n, buf.shape[0])
+    return buf[:n].cpu().numpy().view(HARMONIC_DTYPE).reshape(-1)
+
 
 def _stream_handle(stream) -> int:
     import torch

@@ -7,3 +7,4 @@ from .inputs import (ArraySpec, Chirp, batch_trials, log_uniform_lengths, make_i
                      make_series, poisson_requests, single_ska, single_small)
 from .templates import (CENTRE, FRAME, ZMAX, response, response_quadrature,  # noqa: F401
                         template_bank, template_taps)
+from .planes import add_train, noise_plane, pulsar  # noqa: F401

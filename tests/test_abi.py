@@ -93,3 +93,23 @@ def test_product_package_never_imports_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "fdas_oracle" not in src, fn
+
+
+def test_harmonic_sum_argument_errors_without_gpu(lib):
+    import ctypes
+    import paper_1805_12280_gb300 as fd
+    bad = fd.fdas.FDAS_ERR_INVALID_ARG
+    thr = (ctypes.c_float * 6)(7, 10, 16, 25, 40, 66)
+    P, cnt, cand = ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(1024)   # never dereferenced
+    ok = dict(plane=P, m=85, n=1000, bin0=210, H=8, thr=thr, cand=cand, max_cand=10, count=cnt)
+
+    def call(**kw):
+        a = {**ok, **kw}
+        return lib.fdas_harmonic_sum(a["plane"], a["m"], a["n"], a["bin0"], a["H"], a["thr"], a["cand"],
+                                     a["max_cand"], a["count"], None)
+    for kw in (dict(plane=None), dict(count=None), dict(thr=None), dict(cand=None),
+               dict(m=84), dict(m=0), dict(n=0), dict(bin0=1000), dict(bin0=-1),
+               dict(H=3), dict(H=64), dict(H=0), dict(max_cand=-1),
+               dict(plane=ctypes.c_void_p(258)), dict(count=ctypes.c_void_p(516))):
+        assert call(**kw) == bad, kw
+    assert b"power of two" in (call(H=3), lib.fdas_last_error())[1]
