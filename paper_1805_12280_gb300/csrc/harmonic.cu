@@ -9,12 +9,16 @@
 // is defined where |h z| <= c and bin0 + h r <= n - 1, and every S_h above its level's
 // threshold becomes a candidate.
 //
-// One thread per fundamental: the H loads of its harmonics are issued together (predicated
-// on the harmonic lying inside the plane), then added in the order k = 1, 2, .., the running
-// sum compared with the threshold at every power of two.  A block takes tiles of 2048
-// consecutive fundamentals of one row (the k = 1 loads of a warp are one 128-byte line; the
-// k-th are a k-strided gather, served by L2 for the neighbouring warps of the tile); its
-// crossings are staged in shared memory and reserved in the output with one atomic per tile.
+// A thread takes Q fundamentals of one row, 256 apart (Q H = 64 for H >= 8, Q = 8 below):
+// all Q H loads of their harmonics are issued before the first is used (predicated on the
+// harmonic lying inside the plane), then each sum is formed in the order k = 1, 2, .., the
+// running sum compared with the threshold at every power of two.  A block takes tiles of
+// 256 Q consecutive fundamentals of one row (the k = 1 loads of a warp are one 128-byte
+// line; the k-th are a k-strided gather over k lines); its crossings are staged in shared
+// memory and reserved in the output with one atomic per tile.  The kernel is bound by its
+// integer work per load, so for planes narrower than 2^31 columns each harmonic k has one
+// base address per tile, the thread's Q loads sit at fixed offsets 256 k q from it, and the
+// test "bin0 + k r inside the plane" is one 32-bit compare against r_lim[k] = (n-1-bin0)/k.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,8 +30,6 @@ namespace fdas {
 namespace {
 
 constexpr int kHsThreads = 256;
-constexpr int kHsPerThread = 8;                      // fundamentals per thread and tile
-constexpr int64_t kHsTile = kHsThreads * kHsPerThread;
 constexpr int kHsStage = 256;                        // records staged per block and tile
 constexpr int kHsMaxLevels = 6;                      // h = 1 .. 32
 
@@ -35,12 +37,25 @@ struct HsThresholds {
     float t[kHsMaxLevels];
 };
 
+struct HsLimits {   // r_lim[k] = (n - 1 - bin0) / k: harmonic k of r lies in the plane iff r <= r_lim[k]
+    int r_lim[33];
+};
+
+// fundamentals per thread and tile: loads in flight per thread Q H = 64 (8 for H = 1)
+template <int H>
+__host__ __device__ constexpr int hs_per_thread()
+{
+    return H <= 8 ? 8 : 64 / H;
+}
+
 template <int H>
 __global__ void __launch_bounds__(kHsThreads) harmonic_kernel(const float *__restrict__ P, int m, int64_t n,
                                                               int64_t bin0, int64_t tiles_per_row, HsThresholds thr,
                                                               fdas_harmonic_candidate *__restrict__ out,
                                                               int64_t max_cand, unsigned long long *__restrict__ count)
 {
+    constexpr int Q = hs_per_thread<H>();
+    constexpr int64_t TILE = (int64_t)kHsThreads * Q;
     __shared__ fdas_harmonic_candidate stage[kHsStage];
     __shared__ unsigned n_staged, n_flush;
     __shared__ unsigned long long flush_base;
@@ -52,29 +67,107 @@ __global__ void __launch_bounds__(kHsThreads) harmonic_kernel(const float *__res
         const int z = y - c;
         const int az = z < 0 ? -z : z;
         const int kz = az == 0 ? H : min(H, c / az);   // harmonics whose drift k z lies in the plane
-        const int64_t r0 = 1 + (tile - (int64_t)y * tiles_per_row) * kHsTile;
+        const int64_t r0 = 1 + (tile - (int64_t)y * tiles_per_row) * TILE + threadIdx.x;
         const int64_t origin = (int64_t)c * n + bin0;   // cell of k = 0
         const int64_t step_z = (int64_t)z * n;
         if (threadIdx.x == 0) n_staged = 0;
         __syncthreads();
-#pragma unroll 1
-        for (int q = 0; q < kHsPerThread; ++q) {
-            const int64_t r = r0 + q * kHsThreads + threadIdx.x;
-            if (r > rmax) break;
+        float v[Q][H];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t r = r0 + q * kHsThreads;
             const int64_t step = step_z + r;   // from harmonic k to k + 1
-            float v[H];
 #pragma unroll
             for (int k = 1; k <= H; ++k) {
-                const bool in = k <= kz && (int64_t)k * r <= rmax;
-                v[k - 1] = in ? __ldg(P + origin + (int64_t)k * step) : 0.f;
+                const bool in = k <= kz && (int64_t)k * r <= rmax;   // r <= rmax is the case k = 1
+                v[q][k - 1] = in ? __ldg(P + origin + (int64_t)k * step) : 0.f;
             }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t r = r0 + q * kHsThreads;
             float acc = 0.f;
 #pragma unroll
             for (int k = 1; k <= H; ++k) {
-                acc += v[k - 1];
+                acc += v[q][k - 1];
                 if ((k & (k - 1)) == 0) {   // level h = k
                     const int j = 31 - __clz(k);
                     if (k <= kz && (int64_t)k * r <= rmax && acc > thr.t[j]) {
+                        fdas_harmonic_candidate rec;
+                        rec.tpl = y;
+                        rec.power = acc;
+                        rec.bin = bin0 + r;
+                        rec.nharm = k;
+                        rec.reserved = 0;
+                        const unsigned slot = atomicAdd(&n_staged, 1u);
+                        if (slot < (unsigned)kHsStage) {
+                            stage[slot] = rec;
+                        } else {   // staging full: reserve this record on its own
+                            const unsigned long long at = atomicAdd(count, 1ull);
+                            if ((long long)at < max_cand) out[at] = rec;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned ns = min(n_staged, (unsigned)kHsStage);
+            n_flush = ns;
+            flush_base = ns ? atomicAdd(count, (unsigned long long)ns) : 0ull;
+        }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < n_flush; i += kHsThreads)
+            if ((long long)(flush_base + i) < max_cand) out[flush_base + i] = stage[i];
+        __syncthreads();   // the stage is read before the next tile refills it
+    }
+}
+
+// Planes of fewer than 2^31 columns: fundamentals, bins and the in-row offsets are 32-bit.
+template <int H>
+__global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const float *__restrict__ P, int m, int n,
+                                                                     int bin0, int tiles_per_row, HsThresholds thr,
+                                                                     HsLimits lim,
+                                                                     fdas_harmonic_candidate *__restrict__ out,
+                                                                     int64_t max_cand,
+                                                                     unsigned long long *__restrict__ count)
+{
+    constexpr int Q = hs_per_thread<H>();
+    constexpr int TILE = kHsThreads * Q;
+    __shared__ fdas_harmonic_candidate stage[kHsStage];
+    __shared__ unsigned n_staged, n_flush;
+    __shared__ unsigned long long flush_base;
+    const int c = (m - 1) / 2;
+    const int64_t tiles = (int64_t)m * tiles_per_row;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int y = (int)(tile / tiles_per_row);
+        const int z = y - c;
+        const int az = z < 0 ? -z : z;
+        const int kz = az == 0 ? H : min(H, c / az);   // harmonics whose drift k z lies in the plane
+        const int r0 = 1 + (int)(tile - (int64_t)y * tiles_per_row) * TILE + (int)threadIdx.x;
+        if (threadIdx.x == 0) n_staged = 0;
+        __syncthreads();
+        float v[Q][H];
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            // cell (c + k z, bin0 + k r0); read only where the harmonic lies in the plane
+            const float *base = P + ((int64_t)(c + k * z) * n + bin0 + (int64_t)k * r0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const bool in = k <= kz && r0 + q * kHsThreads <= lim.r_lim[k];
+                v[q][k - 1] = in ? __ldg(base + k * kHsThreads * q) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = r0 + q * kHsThreads;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                acc += v[q][k - 1];
+                if ((k & (k - 1)) == 0) {   // level h = k
+                    const int j = 31 - __clz(k);
+                    if (k <= kz && r <= lim.r_lim[k] && acc > thr.t[j]) {
                         fdas_harmonic_candidate rec;
                         rec.tpl = y;
                         rec.power = acc;
@@ -110,17 +203,28 @@ cudaError_t launch_h(const float *P, int m, int64_t n, int64_t bin0, const HsThr
                      fdas_harmonic_candidate *out, int64_t max_cand, unsigned long long *count, cudaStream_t s)
 {
     const int64_t rmax = n - 1 - bin0;
-    const int64_t tiles_per_row = (rmax + kHsTile - 1) / kHsTile;
+    constexpr int64_t TILE = (int64_t)kHsThreads * hs_per_thread<H>();
+    const int64_t tiles_per_row = (rmax + TILE - 1) / TILE;
     const int64_t tiles = (int64_t)m * tiles_per_row;
+    // 32-bit fundamentals and bins, with room for the last tile's overhang past rmax
+    const bool narrow = n <= (((int64_t)1 << 31) - ((int64_t)1 << 16));
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harmonic_kernel<H>, kHsThreads, 0)) != cudaSuccess)
-        return e;
+    e = narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harmonic_kernel_narrow<H>, kHsThreads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harmonic_kernel<H>, kHsThreads, 0);
+    if (e != cudaSuccess) return e;
     const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(tiles < resident ? tiles : resident);
-    harmonic_kernel<H><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count);
+    if (narrow) {
+        HsLimits lim{};
+        for (int k = 1; k <= 32; ++k) lim.r_lim[k] = (int)(rmax / k);
+        harmonic_kernel_narrow<H><<<grid, kHsThreads, 0, s>>>(P, m, (int)n, (int)bin0, (int)tiles_per_row, thr, lim,
+                                                              out, max_cand, count);
+    } else {
+        harmonic_kernel<H><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count);
+    }
     return cudaGetLastError();
 }
 

@@ -188,3 +188,22 @@ def test_plane_beyond_2_31_elements(fd):
     have = set(zip(got["nharm"].tolist(), got["tpl"].tolist(), got["bin"].tolist()))
     assert count == len(want) and have == want
     assert np.all(got["power"] == got["nharm"])
+
+
+def test_row_beyond_2_31_columns(fd):
+    """One row of 2^31 + 2^20 bins (8.6 GB), past the 32-bit column range: the 64-bit form
+    of the kernel.  A unit train at multiples of the prime r0 = 268566509 reaches columns
+    above 2^31; sums and crossings as in the three-row case."""
+    n, r0, H = (1 << 31) + (1 << 20), 268566509, 8
+    assert all(r0 % d for d in range(2, int(r0 ** 0.5) + 1))
+    P = torch.zeros((1, n), dtype=torch.float32, device="cuda")
+    for k in range(1, H + 1):
+        P[0, k * r0] = 1.0
+    assert H * r0 > 2 ** 31
+    got, count = _run(fd, P, 0, H, [h - 0.5 for h in (1, 2, 4, 8)], 1024)
+    del P
+    torch.cuda.empty_cache()
+    want = {(h, 0, j * r0) for h in (1, 2, 4, 8) for j in range(1, H + 1) if h * j <= H}
+    have = set(zip(got["nharm"].tolist(), got["tpl"].tolist(), got["bin"].tolist()))
+    assert count == len(want) and have == want
+    assert np.all(got["power"] == got["nharm"])
