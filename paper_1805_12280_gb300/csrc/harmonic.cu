@@ -124,19 +124,40 @@ __global__ void __launch_bounds__(kHsThreads) harmonic_kernel(const float *__res
 }
 
 // Planes of fewer than 2^31 columns: fundamentals, bins and the in-row offsets are 32-bit.
+// Crossings are staged per warp (no block barrier: each warp runs its tiles at its own pace)
+// and a warp reserves its staged records with one atomic once 32 or more are waiting.
+constexpr int kWarpStage = 64, kWarpFlush = 32;
+
+__device__ __forceinline__ void warp_flush(fdas_harmonic_candidate *stage, unsigned *n_staged, int lane,
+                                           fdas_harmonic_candidate *__restrict__ out, int64_t max_cand,
+                                           unsigned long long *__restrict__ count)
+{
+    const unsigned ns = min(*n_staged, (unsigned)kWarpStage);
+    unsigned long long base = 0;
+    if (lane == 0 && ns) base = atomicAdd(count, (unsigned long long)ns);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned i = lane; i < ns; i += 32)
+        if ((long long)(base + i) < max_cand) out[base + i] = stage[i];
+    __syncwarp();
+    if (lane == 0) *n_staged = 0;
+    __syncwarp();
+}
+
 template <int H>
 __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const float *__restrict__ P, int m, int n,
-                                                                     int bin0, int tiles_per_row, HsThresholds thr,
-                                                                     HsLimits lim,
-                                                                     fdas_harmonic_candidate *__restrict__ out,
-                                                                     int64_t max_cand,
-                                                                     unsigned long long *__restrict__ count)
+                                                                        int bin0, int tiles_per_row, HsThresholds thr,
+                                                                        HsLimits lim,
+                                                                        fdas_harmonic_candidate *__restrict__ out,
+                                                                        int64_t max_cand,
+                                                                        unsigned long long *__restrict__ count)
 {
     constexpr int Q = hs_per_thread<H>();
     constexpr int TILE = kHsThreads * Q;
-    __shared__ fdas_harmonic_candidate stage[kHsStage];
-    __shared__ unsigned n_staged, n_flush;
-    __shared__ unsigned long long flush_base;
+    __shared__ fdas_harmonic_candidate stage[kHsThreads / 32][kWarpStage];
+    __shared__ unsigned n_staged[kHsThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) n_staged[warp] = 0;
+    __syncwarp();
     const int c = (m - 1) / 2;
     const int64_t tiles = (int64_t)m * tiles_per_row;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -145,8 +166,6 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
         const int az = z < 0 ? -z : z;
         const int kz = az == 0 ? H : min(H, c / az);   // harmonics whose drift k z lies in the plane
         const int r0 = 1 + (int)(tile - (int64_t)y * tiles_per_row) * TILE + (int)threadIdx.x;
-        if (threadIdx.x == 0) n_staged = 0;
-        __syncthreads();
         float v[Q][H];
 #pragma unroll
         for (int k = 1; k <= H; ++k) {
@@ -174,9 +193,9 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
                         rec.bin = bin0 + r;
                         rec.nharm = k;
                         rec.reserved = 0;
-                        const unsigned slot = atomicAdd(&n_staged, 1u);
-                        if (slot < (unsigned)kHsStage) {
-                            stage[slot] = rec;
+                        const unsigned slot = atomicAdd(&n_staged[warp], 1u);
+                        if (slot < (unsigned)kWarpStage) {
+                            stage[warp][slot] = rec;
                         } else {   // staging full: reserve this record on its own
                             const unsigned long long at = atomicAdd(count, 1ull);
                             if ((long long)at < max_cand) out[at] = rec;
@@ -185,17 +204,11 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
                 }
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned ns = min(n_staged, (unsigned)kHsStage);
-            n_flush = ns;
-            flush_base = ns ? atomicAdd(count, (unsigned long long)ns) : 0ull;
-        }
-        __syncthreads();
-        for (unsigned i = threadIdx.x; i < n_flush; i += kHsThreads)
-            if ((long long)(flush_base + i) < max_cand) out[flush_base + i] = stage[i];
-        __syncthreads();   // the stage is read before the next tile refills it
+        __syncwarp();
+        if (n_staged[warp] >= (unsigned)kWarpFlush) warp_flush(stage[warp], &n_staged[warp], lane, out, max_cand, count);
     }
+    __syncwarp();
+    if (n_staged[warp]) warp_flush(stage[warp], &n_staged[warp], lane, out, max_cand, count);
 }
 
 template <int H>
