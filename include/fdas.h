@@ -302,8 +302,10 @@ typedef struct {
  *   count_dev   : device unsigned 64-bit counter (8-byte aligned), cleared on `stream`
  *                 before the launch; afterwards the number of crossings, which may exceed
  *                 max_cand (then only max_cand were stored).
- * Runs on the current device; the order of the records is unspecified.  Asynchronous
- * (one memset and at most one kernel launch on `stream`).  Errors: INVALID_ARG, CUDA.
+ * Runs on the current device; the order of the records is unspecified.  Asynchronous: one
+ * memset, then one kernel launch on `stream` per run of rows with the same number
+ * min(max_harm, c / |z|) of harmonics inside the drift range (at most 2 max_harm - 1
+ * launches; none when no fundamental fits).  Errors: INVALID_ARG, CUDA.
  */
 int fdas_harmonic_sum(const float *plane_dev, int n_templates, int64_t n, int64_t bin0, int max_harm,
                       const float *thresholds, fdas_harmonic_candidate *cand_dev, int64_t max_cand,

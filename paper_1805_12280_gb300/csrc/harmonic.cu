@@ -14,15 +14,22 @@
 // harmonic lying inside the plane), then each sum is formed in the order k = 1, 2, .., the
 // running sum compared with the threshold at every power of two.  A block takes tiles of
 // 256 Q consecutive fundamentals of one row (the k = 1 loads of a warp are one 128-byte
-// line; the k-th are a k-strided gather over k lines); its crossings are staged in shared
-// memory and reserved in the output with one atomic per tile.  The kernel is bound by its
-// integer work per load, so for planes narrower than 2^31 columns each harmonic k has one
-// base address per tile, the thread's Q loads sit at fixed offsets 256 k q from it, and the
-// test "bin0 + k r inside the plane" is one 32-bit compare against r_lim[k] = (n-1-bin0)/k.
+// line; the k-th are a k-strided gather over k lines); in the 64-bit kernel its crossings
+// are staged per block and reserved in the output with one atomic per tile.  The kernel is bound by
+// instruction issue, so for planes narrower than 2^31 columns: rows are launched in runs of
+// equal kz = min(H, c / |z|) (the harmonics whose drift lies in the plane), each run by a
+// kernel compiled for exactly kz harmonics; each harmonic k has one base address per tile,
+// the thread's Q loads sit at fixed offsets 256 k q from it, and the test "bin0 + k r inside
+// the plane" is one 32-bit compare against r_lim[k] = (n-1-bin0)/k; crossings are staged per
+// warp, with no block barrier.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <array>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
+#include <utility>
 
 #include "fdas_internal.cuh"
 
@@ -143,14 +150,17 @@ __device__ __forceinline__ void warp_flush(fdas_harmonic_candidate *stage, unsig
     __syncwarp();
 }
 
-template <int H>
+// One launch per run of rows with the same number KZ = min(H, c / |z|) of harmonics inside
+// the plane's drift range, compiled for exactly that many: no work on harmonics a row lacks.
+template <int KZ>
 __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const float *__restrict__ P, int m, int n,
-                                                                        int bin0, int tiles_per_row, HsThresholds thr,
-                                                                        HsLimits lim,
+                                                                        int bin0, int y0, int nrows, int tiles_per_row,
+                                                                        HsThresholds thr, HsLimits lim,
                                                                         fdas_harmonic_candidate *__restrict__ out,
                                                                         int64_t max_cand,
                                                                         unsigned long long *__restrict__ count)
 {
+    constexpr int H = KZ;
     constexpr int Q = hs_per_thread<H>();
     constexpr int TILE = kHsThreads * Q;
     __shared__ fdas_harmonic_candidate stage[kHsThreads / 32][kWarpStage];
@@ -159,13 +169,12 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
     if (lane == 0) n_staged[warp] = 0;
     __syncwarp();
     const int c = (m - 1) / 2;
-    const int64_t tiles = (int64_t)m * tiles_per_row;
+    const int64_t tiles = (int64_t)nrows * tiles_per_row;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int y = (int)(tile / tiles_per_row);
+        const int yr = (int)(tile / tiles_per_row);
+        const int y = y0 + yr;
         const int z = y - c;
-        const int az = z < 0 ? -z : z;
-        const int kz = az == 0 ? H : min(H, c / az);   // harmonics whose drift k z lies in the plane
-        const int r0 = 1 + (int)(tile - (int64_t)y * tiles_per_row) * TILE + (int)threadIdx.x;
+        const int r0 = 1 + (int)(tile - (int64_t)yr * tiles_per_row) * TILE + (int)threadIdx.x;
         float v[Q][H];
 #pragma unroll
         for (int k = 1; k <= H; ++k) {
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
             const float *base = P + ((int64_t)(c + k * z) * n + bin0 + (int64_t)k * r0);
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const bool in = k <= kz && r0 + q * kHsThreads <= lim.r_lim[k];
+                const bool in = r0 + q * kHsThreads <= lim.r_lim[k];
                 v[q][k - 1] = in ? __ldg(base + k * kHsThreads * q) : 0.f;
             }
         }
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
                 acc += v[q][k - 1];
                 if ((k & (k - 1)) == 0) {   // level h = k
                     const int j = 31 - __clz(k);
-                    if (k <= kz && r <= lim.r_lim[k] && acc > thr.t[j]) {
+                    if (r <= lim.r_lim[k] && acc > thr.t[j]) {
                         fdas_harmonic_candidate rec;
                         rec.tpl = y;
                         rec.power = acc;
@@ -211,32 +220,77 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
     if (n_staged[warp]) warp_flush(stage[warp], &n_staged[warp], lane, out, max_cand, count);
 }
 
-template <int H>
-cudaError_t launch_h(const float *P, int m, int64_t n, int64_t bin0, const HsThresholds &thr,
-                     fdas_harmonic_candidate *out, int64_t max_cand, unsigned long long *count, cudaStream_t s)
+using NarrowKernel = void (*)(const float *, int, int, int, int, int, int, HsThresholds, HsLimits,
+                              fdas_harmonic_candidate *, int64_t, unsigned long long *);
+
+template <int... K>
+constexpr std::array<NarrowKernel, sizeof...(K)> narrow_table(std::integer_sequence<int, K...>)
 {
-    const int64_t rmax = n - 1 - bin0;
-    constexpr int64_t TILE = (int64_t)kHsThreads * hs_per_thread<H>();
-    const int64_t tiles_per_row = (rmax + TILE - 1) / TILE;
-    const int64_t tiles = (int64_t)m * tiles_per_row;
-    // 32-bit fundamentals and bins, with room for the last tile's overhang past rmax
-    const bool narrow = n <= (((int64_t)1 << 31) - ((int64_t)1 << 16));
+    return {&harmonic_kernel_narrow<K + 1>...};
+}
+
+// harmonic_kernel_narrow<KZ> for KZ = 1 .. 32
+constexpr std::array<NarrowKernel, 32> kNarrow = narrow_table(std::make_integer_sequence<int, 32>{});
+
+cudaError_t resident_grid(const void *fn, int64_t tiles, unsigned *grid)
+{
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    e = narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harmonic_kernel_narrow<H>, kHsThreads, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, harmonic_kernel<H>, kHsThreads, 0);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kHsThreads, 0)) != cudaSuccess) return e;
     const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const unsigned grid = (unsigned)(tiles < resident ? tiles : resident);
-    if (narrow) {
+    *grid = (unsigned)(tiles < resident ? tiles : resident);
+    return cudaSuccess;
+}
+
+cudaError_t launch_hs(int H, const float *P, int m, int64_t n, int64_t bin0, const HsThresholds &thr,
+                      fdas_harmonic_candidate *out, int64_t max_cand, unsigned long long *count, cudaStream_t s)
+{
+    const int64_t rmax = n - 1 - bin0;
+    const int c = (m - 1) / 2;
+    cudaError_t e;
+    unsigned grid = 0;
+    // 32-bit fundamentals and bins, with room for the last tile's overhang past rmax
+    if (n <= (((int64_t)1 << 31) - ((int64_t)1 << 16))) {
         HsLimits lim{};
         for (int k = 1; k <= 32; ++k) lim.r_lim[k] = (int)(rmax / k);
-        harmonic_kernel_narrow<H><<<grid, kHsThreads, 0, s>>>(P, m, (int)n, (int)bin0, (int)tiles_per_row, thr, lim,
-                                                              out, max_cand, count);
-    } else {
-        harmonic_kernel<H><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count);
+        auto kz_of = [&](int y) { const int az = std::abs(y - c); return az == 0 ? H : std::min(H, c / az); };
+        for (int y0 = 0; y0 < m;) {   // runs of rows with the same kz
+            const int kz = kz_of(y0);
+            int y1 = y0 + 1;
+            while (y1 < m && kz_of(y1) == kz) ++y1;
+            const NarrowKernel fn = kNarrow[kz - 1];
+            const int64_t tile = (int64_t)kHsThreads * (kz <= 8 ? 8 : 64 / kz);
+            const int64_t tiles_per_row = (rmax + tile - 1) / tile;
+            if ((e = resident_grid((const void *)fn, (int64_t)(y1 - y0) * tiles_per_row, &grid)) != cudaSuccess)
+                return e;
+            fn<<<grid, kHsThreads, 0, s>>>(P, m, (int)n, (int)bin0, y0, y1 - y0, (int)tiles_per_row, thr, lim, out,
+                                           max_cand, count);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            y0 = y1;
+        }
+        return cudaSuccess;
+    }
+    const void *fn = nullptr;
+    int64_t tile = 0;
+    switch (H) {
+    case 1: fn = (const void *)harmonic_kernel<1>; tile = kHsThreads * hs_per_thread<1>(); break;
+    case 2: fn = (const void *)harmonic_kernel<2>; tile = kHsThreads * hs_per_thread<2>(); break;
+    case 4: fn = (const void *)harmonic_kernel<4>; tile = kHsThreads * hs_per_thread<4>(); break;
+    case 8: fn = (const void *)harmonic_kernel<8>; tile = kHsThreads * hs_per_thread<8>(); break;
+    case 16: fn = (const void *)harmonic_kernel<16>; tile = kHsThreads * hs_per_thread<16>(); break;
+    default: fn = (const void *)harmonic_kernel<32>; tile = kHsThreads * hs_per_thread<32>(); break;
+    }
+    const int64_t tiles_per_row = (rmax + tile - 1) / tile;
+    if ((e = resident_grid(fn, (int64_t)m * tiles_per_row, &grid)) != cudaSuccess) return e;
+    switch (H) {
+    case 1: harmonic_kernel<1><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count); break;
+    case 2: harmonic_kernel<2><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count); break;
+    case 4: harmonic_kernel<4><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count); break;
+    case 8: harmonic_kernel<8><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count); break;
+    case 16: harmonic_kernel<16><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count); break;
+    default: harmonic_kernel<32><<<grid, kHsThreads, 0, s>>>(P, m, n, bin0, tiles_per_row, thr, out, max_cand, count); break;
     }
     return cudaGetLastError();
 }
@@ -273,14 +327,7 @@ extern "C" int fdas_harmonic_sum(const float *plane_dev, int n_templates, int64_
     cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return hs_cuda(e, "clear candidate counter");
     if (n - 1 - bin0 < 1) return FDAS_OK;   // no fundamental r >= 1 inside the plane
-    switch (max_harm) {
-    case 1: e = launch_h<1>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
-    case 2: e = launch_h<2>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
-    case 4: e = launch_h<4>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
-    case 8: e = launch_h<8>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
-    case 16: e = launch_h<16>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
-    default: e = launch_h<32>(plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s); break;
-    }
+    e = launch_hs(max_harm, plane_dev, n_templates, n, bin0, thr, cand_dev, max_cand, count_dev, s);
     if (e != cudaSuccess) return hs_cuda(e, "harmonic-sum launch");
     return FDAS_OK;
 }
