@@ -513,6 +513,10 @@ def bench_harmonic(fd, h, dev, xd, reps=20):
                                     "plane_read_gbs": plane_bytes / (ms / 1e3) / 1e9,
                                     "hbm_frac": plane_bytes / (ms / 1e3) / 1e9 / peak,
                                     "thresholds": [round(t, 3) for t in thr]}
+            traffic = profile_traffic("harmonic", f"harmonic_sum_h{H}_n2p22_traffic.json")
+            if traffic:   # the bytes the launches of one call move (ncu record), at this call's duration
+                res[f"max_harm_{H}"].update({"traffic": traffic, "traffic_gbs": traffic / (ms / 1e3) / 1e9,
+                                             "traffic_hbm_frac": traffic / (ms / 1e3) / 1e9 / peak})
 
         def chain():
             plan.convolve(xd, plane, stream)
@@ -743,7 +747,8 @@ def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=3
 KERNEL_SOURCES = {"fp32": ("ols_fp32.cu", "ols_common.cuh", "fft_regs.cuh", "ptx.cuh", "tmem.cuh", "fdas_internal.cuh",
                            "plan_kernels.cu"),
                   "tc": ("ols_tc.cu", "ols_common.cuh", "fft_regs.cuh", "fft_split.cuh", "ptx.cuh", "tmem.cuh",
-                         "fdas_internal.cuh", "plan_kernels.cu")}
+                         "fdas_internal.cuh", "plan_kernels.cu"),
+                  "harmonic": ("harmonic.cu", "fdas_internal.cuh")}
 
 
 def _code_only(text: str) -> str:
@@ -782,9 +787,10 @@ def kernel_sources_sha256(precision: str) -> str:
     return h.hexdigest()
 
 
-def profile_traffic(precision: str = "fp32"):
-    """DRAM bytes per launch from the committed ncu record, if it matches this kernel's sources."""
-    path = os.path.join(ROOT, "profiles", f"ols_{precision}_L2048_n2p22_traffic.json")
+def profile_traffic(precision: str = "fp32", record: str | None = None):
+    """DRAM bytes per launch (per call for the harmonic sums) from the committed ncu record,
+    if it matches the kernel's sources."""
+    path = os.path.join(ROOT, "profiles", record or f"ols_{precision}_L2048_n2p22_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
