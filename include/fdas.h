@@ -305,7 +305,8 @@ typedef struct {
  * Runs on the current device; the order of the records is unspecified.  Asynchronous: one
  * memset, then one kernel launch on `stream` per run of rows with the same number
  * min(max_harm, c / |z|) of harmonics inside the drift range (at most 2 max_harm - 1
- * launches; none when no fundamental fits).  Errors: INVALID_ARG, CUDA.
+ * launches; a single launch for rows of more than 2^31 - 2^16 bins; none when no fundamental
+ * fits).  Errors: INVALID_ARG, CUDA.
  */
 int fdas_harmonic_sum(const float *plane_dev, int n_templates, int64_t n, int64_t bin0, int max_harm,
                       const float *thresholds, fdas_harmonic_candidate *cand_dev, int64_t max_cand,

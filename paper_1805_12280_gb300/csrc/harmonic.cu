@@ -261,7 +261,7 @@ cudaError_t launch_hs(int H, const float *P, int m, int64_t n, int64_t bin0, con
             int y1 = y0 + 1;
             while (y1 < m && kz_of(y1) == kz) ++y1;
             const NarrowKernel fn = kNarrow[kz - 1];
-            const int64_t tile = (int64_t)kHsThreads * (kz <= 8 ? 8 : 64 / kz);
+            const int64_t tile = (int64_t)kHsThreads * (kz <= 8 ? 8 : 64 / kz);   // hs_per_thread<kz>()
             const int64_t tiles_per_row = (rmax + tile - 1) / tile;
             if ((e = resident_grid((const void *)fn, (int64_t)(y1 - y0) * tiles_per_row, &grid)) != cudaSuccess)
                 return e;
