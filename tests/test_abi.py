@@ -113,3 +113,14 @@ def test_harmonic_sum_argument_errors_without_gpu(lib):
                dict(plane=ctypes.c_void_p(258)), dict(count=ctypes.c_void_p(516))):
         assert call(**kw) == bad, kw
     assert b"power of two" in (call(H=3), lib.fdas_last_error())[1]
+
+
+def test_harmonic_binding_checks_without_gpu():
+    torch = pytest.importorskip("torch")
+    import paper_1805_12280_gb300 as fd
+    with pytest.raises(ValueError):
+        fd.harmonic_sum(torch.zeros((85, 100), dtype=torch.float32), 10, 8)        # host tensor
+    with pytest.raises(ValueError):
+        fd.harmonic_sum(torch.zeros(100, dtype=torch.float32), 10, 8)              # not 2-D
+    with pytest.raises(ValueError):
+        fd.harmonic_sum(torch.zeros((85, 100), dtype=torch.float64), 10, 8)        # not float32

@@ -117,3 +117,25 @@ def test_invalid_arguments():
     for args in [(P, 0, 3), (P, 0, 64), (P, 50, 2), (P, -1, 2), (np.zeros((8, 50), np.float32), 0, 2)]:
         with pytest.raises(ValueError):
             oracle.harmonic_sums(*args)
+
+
+def test_candidate_list_truncation_and_threads():
+    n, bin0, H = 900, 3, 8
+    P = synth.noise_plane(M, n, 21)
+    thr = [-1.0] * 4
+    full = oracle.harmonic_candidates(P, bin0, H, thr)
+    total = full["bin"].size
+    assert total == int((~np.isnan(oracle.harmonic_sums(P, bin0, H))).sum())
+    n0 = oracle.threads()
+    try:
+        oracle.set_threads(1)
+        one = oracle.harmonic_candidates(P, bin0, H, thr)
+        s1 = oracle.harmonic_sums(P, bin0, H)
+        oracle.set_threads(max(2, n0))
+        many = oracle.harmonic_candidates(P, bin0, H, thr)
+        sm = oracle.harmonic_sums(P, bin0, H)
+    finally:
+        oracle.set_threads(n0)
+    for k in full:
+        assert np.array_equal(one[k], many[k])
+    assert np.array_equal(s1, sm, equal_nan=True)

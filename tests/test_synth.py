@@ -88,3 +88,14 @@ def test_workload_specs():
     assert len({s.seed for s in b}) == 64
     t, reqs = synth.poisson_requests(100)
     assert np.all(np.diff(t) > 0) and len(reqs) == 100
+
+
+def test_pulsar_harmonics_and_planes():
+    s = synth.pulsar(1 << 14, 5, 1000.5, 2.0, [0.05, 0.04, 0.03])
+    assert [(c.r, c.z, c.a) for c in s.chirps] == [(1000.5, 2.0, 0.05), (2001.0, 4.0, 0.04), (3001.5, 6.0, 0.03)]
+    P = synth.noise_plane(5, 20000, 9)
+    assert P.dtype == np.float32 and P.shape == (5, 20000) and P.min() >= 0
+    assert abs(P.mean() - 1.0) < 0.02 and abs(P.var() - 1.0) < 0.05        # unit exponential
+    np.testing.assert_array_equal(P, synth.noise_plane(5, 20000, 9))
+    Z = synth.add_train(np.zeros((5, 100), np.float32), 10, 7, 1, [3.0, 2.0, 1.0])
+    assert Z[3, 17] == 3.0 and Z[4, 24] == 2.0 and Z.sum() == 5.0            # k = 3 falls outside the rows
