@@ -203,6 +203,21 @@ def time_oracle_sample(x, h, seg_len, target_s):
     return sample, dt, oracle.threads(), runs
 
 
+def time_oracle_harmonic(m, n_full, bin0, max_harm, thresholds, cols=1 << 20, seed=1):
+    """Time the FP64 harmonic-sum oracle (C, OpenMP) on a seeded m x cols noise plane and
+    scale to the m x n_full plane: the sums read a number of cells proportional to the plane."""
+    import oracle
+    oracle.build()
+    P = synth.noise_plane(m, cols, seed)
+    t0 = time.perf_counter()
+    found = oracle.harmonic_candidates(P, bin0, max_harm, thresholds)
+    dt = time.perf_counter() - t0
+    per_array_s = dt * (n_full - 1 - bin0) / (cols - 1 - bin0)
+    return {"value": 1.0 / per_array_s, "unit": "arrays/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP64 harmonic-sum oracle (C, OpenMP) on a seeded {m} x {cols} noise plane "
+                      f"({found['bin'].size} crossings, {dt:.2f} s), scaled by cells to {m} x {n_full}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -357,7 +372,7 @@ def run_fdas(args):
         del out
         torch.cuda.empty_cache()
         forms = {"tensor_core": bench_tc(fd, h, dev, xd), "candidates": bench_candidates(fd, h, dev, xd, x),
-                 "harmonic_sum": bench_harmonic(fd, h, dev, xd),
+                 "harmonic_sum": bench_harmonic(fd, h, dev, xd, oracle_beside=not args.no_cpu_baseline),
                  "template_groups": bench_groups(fd, h, dev, xd),
                  "library_unfused_ols": bench_library_ols(h, dev, xd),
                  "full_fdfir": bench_fdfir(fd, h, dev, xd),
@@ -489,7 +504,7 @@ def bench_candidates(fd, h, dev, xd, x_host, reps=50, threshold=7.0):
     return res
 
 
-def bench_harmonic(fd, h, dev, xd, reps=20):
+def bench_harmonic(fd, h, dev, xd, reps=20, oracle_beside=True):
     """Harmonic summing (fdas_harmonic_sum) of the headline array's plane: sums of 8 and 16
     harmonics at bin k r, drift k z, thresholds h + 6 sqrt(h); and the chain plane + sums."""
     import torch
@@ -555,6 +570,8 @@ def bench_harmonic(fd, h, dev, xd, reps=20):
                                            "api": "fdas_convolve + fdas_harmonic_sum, pinned host input, records down"}
         res["peak_kind"] = peak_kind
         plan.status(stream)
+    if oracle_beside:   # the oracle beside the kernel (8 harmonics, same thresholds)
+        res["max_harm_8"]["cpu_baseline"] = time_oracle_harmonic(m, n, bin0, 8, fd.harmonic_thresholds(8))
     return res
 
 

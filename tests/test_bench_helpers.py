@@ -68,3 +68,10 @@ def test_harmonic_defaults():
     assert fd.harmonic_levels(1) == [1] and fd.harmonic_levels(32) == [1, 2, 4, 8, 16, 32]
     thr = fd.harmonic_thresholds(8)
     assert thr[0] == 7.0 and thr[2] == 16.0 and thr[3] == pytest.approx(8 + 6 * 8 ** 0.5)
+
+
+def test_oracle_harmonic_timing_record():
+    b = _bench()
+    rec = b.time_oracle_harmonic(85, 1 << 16, 210, 8, [7.0, 10.49, 16.0, 24.97], cols=1 << 13)
+    assert rec["kind"] == "oracle" and rec["unit"] == "arrays/s" and rec["cores"] >= 1
+    assert rec["value"] > 0 and "85 x 8192" in rec["sample"]
