@@ -276,7 +276,7 @@ def run_fdas(args):
     x = synth.make_input(spec)
     h, _ = synth.template_bank()
     n, m = x.size, h.shape[0]
-    prec = fd.FDAS_PREC_TC_FP16 if args.precision == "tc" else fd.FDAS_PREC_FP32
+    prec = {"tc": fd.FDAS_PREC_TC_FP16, "tc2": fd.FDAS_PREC_TC_DFT2}.get(args.precision, fd.FDAS_PREC_FP32)
     plan = fd.Plan(h, n_max=n, seg_len=args.seg_len, tpl_per_cta=args.tpl_per_cta, precision=prec)
     stream = torch.cuda.current_stream(dev)
     xd = torch.from_numpy(x).to(dev)
@@ -350,11 +350,12 @@ def run_fdas(args):
     traffic = profile_traffic(args.precision) if same_workload else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": f"ols_fp32_kernel<{args.seg_len}>" if args.precision == "fp32" else "ols_tc_kernel",
+                "kernel": {"fp32": f"ols_fp32_kernel<{args.seg_len}>", "tc": "ols_tc_kernel",
+                           "tc2": "ols_tc2_kernel"}[args.precision],
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kern_ms}
 
     # Second roofline: the paper's operation count (Table 1, C = 5) against the FP32 CUDA-core
-    # peak of this GPU (152 SMs x 128 FP32 lanes x 2 flop per FMA x the sampled SM clock).
+    # peak of this GPU (SMs x 128 FP32 lanes x 2 flop per FMA x the sampled SM clock).
     flops = model_flops(n, m, args.seg_len, h.shape[1])
     roofline_alu = {"bound": "alu", "achieved": flops / (kern_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                     "flops_per_launch": flops, "note": "paper operation count (Table 1, C=5); the kernel is "
@@ -382,7 +383,9 @@ def run_fdas(args):
 
     clock_summary = clocks.summary()
     sm_mhz = clock_summary.get("sm_mhz") or clock_summary.get("sm_max_mhz") or 2070.0
-    roofline_alu["peak"] = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roofline_alu["peak"] = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    roofline_alu["sms"] = sms
     roofline_alu["frac"] = roofline_alu["achieved"] / roofline_alu["peak"]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -422,7 +425,7 @@ def bench_tc(fd, h, dev, xd, reps=50):
     out = torch.empty((m, n), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     res = {"workload": "N=2^22, 85 templates, L=2048, G=85 (same array as the headline)"}
-    for name, prec in (("tc_fp16", fd.FDAS_PREC_TC_FP16), ("fp32", fd.FDAS_PREC_FP32)):
+    for name, prec in (("tc_dft2", fd.FDAS_PREC_TC_DFT2), ("tc_fp16", fd.FDAS_PREC_TC_FP16), ("fp32", fd.FDAS_PREC_FP32)):
         with fd.Plan(h, n_max=n, precision=prec) as plan:
             for _ in range(3):
                 plan.convolve(xd, out, stream)
@@ -793,6 +796,8 @@ KERNEL_SOURCES = {"fp32": ("ols_fp32.cu", "ols_common.cuh", "fft_regs.cuh", "ptx
                            "plan_kernels.cu"),
                   "tc": ("ols_tc.cu", "ols_common.cuh", "fft_regs.cuh", "fft_split.cuh", "ptx.cuh", "tmem.cuh",
                          "fdas_internal.cuh", "plan_kernels.cu"),
+                  "tc2": ("ols_tc2.cu", "ols_common.cuh", "fft_regs.cuh", "fft_split.cuh", "ptx.cuh", "tmem.cuh",
+                          "fdas_internal.cuh", "plan_kernels.cu"),
                   "harmonic": ("harmonic.cu", "fdas_internal.cuh")}
 
 
@@ -855,8 +860,9 @@ def main():
     ap.add_argument("--seg-len", type=int, default=2048)
     ap.add_argument("--log2n", type=int, default=22, help="array length 2^log2n (22 = the SKA-sized workload)")
     ap.add_argument("--tpl-per-cta", type=int, default=0)
-    ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
-                    help="segment-kernel arithmetic of the timed steps (tc: tensor-core DFT-GEMM passes)")
+    ap.add_argument("--precision", choices=["fp32", "tc", "tc2"], default="fp32",
+                    help="segment-kernel arithmetic of the timed steps (tc: one radix-16 tensor-core pass; "
+                         "tc2: the whole inverse FFT as two tensor-core DFT-GEMMs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")

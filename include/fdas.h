@@ -43,6 +43,11 @@ extern "C" {
 #define FDAS_PREC_TC_FP16       1     /* the inverse FFT's first radix-16 pass as a tensor-core
                                          DFT-GEMM: fp16 data, fp16 hi/lo-split DFT matrix, FP32
                                          accumulation; the other passes FP32; needs seg_len 2048 */
+#define FDAS_PREC_TC_DFT2       2     /* the whole inverse FFT as two tensor-core DFT-GEMMs
+                                         (2048 = 32 x 64: fp16 operands, FP32 accumulation, the
+                                         product with H_z fused into the first operand, the twiddle
+                                         and |y|^2 on the CUDA cores); the forward FFT FP32 with a
+                                         per-segment power-of-two range scale; needs seg_len 2048 */
 
 typedef struct fdas_plan_s *fdas_plan;
 
@@ -198,7 +203,8 @@ int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *o
  * host; their kernels run in stream order and must not overlap in time: do not
  * issue batches of one plan on two streams that run concurrently.
  * Errors: INVALID_ARG (any entry invalid: nothing is enqueued), UNSUPPORTED (a plan
- * created with group_support), CUDA.
+ * created with group_support, or a plan whose precision this form is not built for;
+ * nothing is enqueued), CUDA.
  */
 int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns,
                         float *const *outs, void *stream);
@@ -225,7 +231,10 @@ int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const in
  * All calls in the process share the one array: calls whose work overlaps on the GPU
  * (different streams, different plans, or different threads without ordering) race
  * on it and must be serialised by the caller.  Asynchronous.
- * Errors: INVALID_ARG, CUDA.
+ * A device reset (cudaDeviceReset) destroys the counter array with the context; the
+ * address looked up before it is not looked up again, so after a reset this entry point
+ * must not be called again in the same process.
+ * Errors: INVALID_ARG, UNSUPPORTED (as fdas_convolve_batch), CUDA.
  */
 int fdas_convolve_batch_noalloc(fdas_plan p, int count, const void *const *ins, const int64_t *ns,
                                 float *const *outs, void *stream);
@@ -345,7 +354,8 @@ typedef struct {
 } fdas_server_report;
 
 /* Create a server (starts its scheduler thread; reserves budget_bytes on the plan's
- * device).  Errors: INVALID_ARG, OOM, CUDA. */
+ * device).  Errors: INVALID_ARG, UNSUPPORTED (a grouped plan, or a plan whose precision the
+ * batched form is not built for), OOM, CUDA. */
 int fdas_server_create(fdas_server *out, fdas_plan plan, const fdas_server_opts *opts);
 
 /* Queue one request.  in_c64_dev: device complex64 [n], 16-byte aligned, valid until

@@ -3,7 +3,7 @@
 The computation lives in ``libfdas.so`` (hand-written CUDA kernels behind the C ABI
 of ``include/fdas.h``); ``fdas`` is its ctypes binding.
 """
-from .fdas import (FDAS_PREC_FP32, FDAS_PREC_TC_FP16, FdasError, Plan, Server, fdas_convolve,  # noqa: F401
+from .fdas import (FDAS_PREC_FP32, FDAS_PREC_TC_DFT2, FDAS_PREC_TC_FP16, FdasError, Plan, Server, fdas_convolve,  # noqa: F401
                    fdas_server_create, fdas_server_destroy, fdas_server_release, fdas_server_stats,
                    fdas_server_submit, fdas_server_wait,
                    candidates_to_numpy, fdas_convolve_batch, fdas_convolve_batch_noalloc,
@@ -18,4 +18,4 @@ __all__ = ["Plan", "Server", "FdasError", "fdas_server_create", "fdas_server_sub
            "fdas_convolve_batch", "fdas_convolve_batch_noalloc", "fdas_convolve_candidates",
            "fdas_convolve_direct", "candidates_to_numpy", "fdas_convolve_host", "fdas_plan_status", "fdas_destroy", "fdas_version",
            "fdas_harmonic_sum", "harmonic_levels", "harmonic_sum", "harmonic_thresholds", "harmonic_to_numpy",
-           "FDAS_PREC_FP32", "FDAS_PREC_TC_FP16"]
+           "FDAS_PREC_FP32", "FDAS_PREC_TC_FP16", "FDAS_PREC_TC_DFT2"]

@@ -104,6 +104,9 @@ struct fdas_plan_s {
     double2 *d_tw64 = nullptr;  // [L] FP64 twiddles
     float4 *d_H = nullptr;      // [M][8][L/16] pre-transformed templates
     unsigned char *d_wtc = nullptr;   // tensor-core form: real 32x32 DFT matrices (hi/lo fp16)
+    unsigned char *d_tc2c = nullptr;  // two-stage tensor-core form: DFT matrices and twiddles
+    unsigned char *d_H16 = nullptr;   // two-stage tensor-core form: fp16 template spectra
+    int eH = 0;                       // their power-of-two scale
     float2 *d_h32 = nullptr;          // raw templates [M][K] (time-domain form)
     // grouped plans: templates permuted into support groups, stored shifted to their first tap
     struct Group {
@@ -142,6 +145,8 @@ void plan_free(fdas_plan p)
     cudaFree(p->d_tw64);
     cudaFree(p->d_H);
     cudaFree(p->d_wtc);
+    cudaFree(p->d_tc2c);
+    cudaFree(p->d_H16);
     cudaFree(p->d_h32);
     cudaFree(p->d_rows);
     cudaFree(p->d_shifts);
@@ -244,6 +249,13 @@ int enqueue_segments(fdas_plan p, const CUtensorMap *map, int64_t n, float *out,
         if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch");
         return FDAS_OK;
     }
+    if (p->precision == FDAS_PREC_TC_DFT2) {
+        fdas::OlsArgs b = a;
+        b.seg_begin = (int)s0;
+        cudaError_t e = fdas::launch_ols_tc2(map, b, p->d_H16, p->d_tc2c, p->eH, (int)(s1 - s0), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch (two-stage tensor-core form)");
+        return FDAS_OK;
+    }
     return launch_range(p, map, a, s0, s1, stream);
 }
 
@@ -340,6 +352,8 @@ int validate_batch(fdas_plan p, int count, const void *const *ins, const int64_t
 {
     if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");
     if (p->d_rows) return fail(FDAS_ERR_UNSUPPORTED, "the batched forms are built for ungrouped plans");
+    if (p->precision != FDAS_PREC_FP32)
+        return fail(FDAS_ERR_UNSUPPORTED, "the batched forms are built for FP32 plans (precision %d)", p->precision);
     if (count < 0 || (count > 0 && (!ins || !ns || !outs))) return fail(FDAS_ERR_INVALID_ARG, "bad batch arrays");
     for (int i = 0; i < count; ++i) {
         int rc = validate_convolve(p, ins[i], ns[i], outs[i]);
@@ -621,6 +635,7 @@ int validate_array(fdas_plan p, const void *in, int64_t n, const float *out)
 
 int plan_templates(fdas_plan p) { return p ? p->M : 0; }
 int plan_grouped(fdas_plan p) { return p && p->d_rows ? 1 : 0; }
+int plan_precision(fdas_plan p) { return p ? p->precision : -1; }
 int *plan_status_word(fdas_plan p) { return p ? p->d_status : nullptr; }
 int64_t plan_n_max(fdas_plan p) { return p ? p->n_max : 0; }
 
@@ -659,10 +674,10 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     if (opts) o = *opts;
     const int L = o.seg_len ? o.seg_len : 2048;
     if (L != 1024 && L != 2048 && L != 4096) return fail(FDAS_ERR_INVALID_ARG, "seg_len %d not in {1024, 2048, 4096}", L);
-    if (o.precision != FDAS_PREC_FP32 && o.precision != FDAS_PREC_TC_FP16)
+    if (o.precision != FDAS_PREC_FP32 && o.precision != FDAS_PREC_TC_FP16 && o.precision != FDAS_PREC_TC_DFT2)
         return fail(FDAS_ERR_UNSUPPORTED, "precision %d not built", o.precision);
-    if (o.precision == FDAS_PREC_TC_FP16 && (L != 2048 || o.autotune))
-        return fail(FDAS_ERR_UNSUPPORTED, "the tensor-core form is built for seg_len 2048 without autotuning");
+    if (o.precision != FDAS_PREC_FP32 && (L != 2048 || o.autotune))
+        return fail(FDAS_ERR_UNSUPPORTED, "the tensor-core forms are built for seg_len 2048 without autotuning");
     if (!templates) return fail(FDAS_ERR_INVALID_ARG, "null templates");
     if (M < 1) return fail(FDAS_ERR_INVALID_ARG, "n_templates=%d < 1", M);
     if (K < 1 || K > L - 4) return fail(FDAS_ERR_INVALID_ARG, "tpl_len=%d outside [1, %d]", K, L - 4);
@@ -708,6 +723,23 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
         if ((e = cudaMalloc(&p->d_wtc, fdas::tc_matrix_bytes())) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc DFT matrices");
         else if ((e = fdas::launch_tc_matrices(p->d_wtc, nullptr)) != cudaSuccess) rc = cuda_fail(e, "DFT matrix kernel");
     }
+    if (rc == FDAS_OK && p->precision == FDAS_PREC_TC_DFT2) {
+        // template scale 2^eH: the largest power of two with 2^eH max_z sum_k |h_z[k]| <= 16,
+        // which bounds every |FFT(h_z)[f]| 2^eH by 16 (fp16 operand range)
+        const float2 *hh = static_cast<const float2 *>(templates);
+        double l1max = 0.0;
+        for (int z = 0; z < M; ++z) {
+            double l1 = 0.0;
+            for (int k = 0; k < K; ++k) l1 += std::hypot((double)hh[(size_t)z * K + k].x, (double)hh[(size_t)z * K + k].y);
+            l1max = std::max(l1max, l1);
+        }
+        p->eH = l1max > 0.0 ? (int)std::floor(std::log2(16.0 / l1max)) : 0;
+        p->eH = std::max(-60, std::min(60, p->eH));
+        if ((e = cudaMalloc(&p->d_tc2c, fdas::tc2_const_bytes())) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc tensor-core constants");
+        else if ((e = cudaMalloc(&p->d_H16, fdas::tc2_template_bytes(M))) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMalloc fp16 template spectra");
+        else if ((e = fdas::launch_tc2_constants(p->d_tc2c, nullptr)) != cudaSuccess) rc = cuda_fail(e, "tensor-core constants kernel");
+    }
     if (rc == FDAS_OK && o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
     p->d_h32 = d_h32;   // kept for the time-domain form
     if (rc == FDAS_OK && o.group_support) {
@@ -730,10 +762,16 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     } else if (rc == FDAS_OK) {
         rc = build_templates(p, d_h32, p->L);
     }
+    if (rc == FDAS_OK && p->precision == FDAS_PREC_TC_DFT2) {
+        if ((e = fdas::launch_tc2_pretransform(d_h32, M, K, p->d_tw64, p->eH, p->d_H16, nullptr)) != cudaSuccess)
+            rc = cuda_fail(e, "fp16 template pre-transform");
+        else if ((e = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_fail(e, "plan-time kernels");
+    }
     if (rc != FDAS_OK) return cleanup_fail(rc);
     p->device_bytes = (int64_t)(sizeof(float2) * p->L + sizeof(double2) * p->L +
                                 sizeof(float4) * (size_t)M * 8 * (p->L / 16) + sizeof(int) + h_bytes +
-                                (p->d_wtc ? fdas::tc_matrix_bytes() : 0) + (p->d_rows ? 2 * sizeof(int) * M : 0));
+                                (p->d_wtc ? fdas::tc_matrix_bytes() : 0) + (p->d_rows ? 2 * sizeof(int) * M : 0) +
+                                (p->d_tc2c ? fdas::tc2_const_bytes() + fdas::tc2_template_bytes(M) : 0));
     *out = p;
     return FDAS_OK;
 }

@@ -107,6 +107,7 @@ void lane_free(Lane *l);
 int validate_array(fdas_plan p, const void *in, int64_t n, const float *out);
 int plan_templates(fdas_plan p);
 int plan_grouped(fdas_plan p);
+int plan_precision(fdas_plan p);      // FDAS_PREC_* of the plan
 int *plan_status_word(fdas_plan p);   // the plan's device status word
 int64_t plan_n_max(fdas_plan p);
 
@@ -128,6 +129,17 @@ cudaError_t launch_tc_matrices(unsigned char *wmat, cudaStream_t s);
 size_t tc_matrix_bytes();
 cudaError_t launch_ols_tc(const CUtensorMap *tmap, const OlsArgs &a, const unsigned char *wmat, int nseg,
                           cudaStream_t s);
+
+// Two-stage tensor-core form (L = 2048): plan constants (the two real DFT matrices and the
+// twiddle table), the fp16 template spectra, and the segment kernel over segments
+// [a.seg_begin, a.seg_begin + nseg).
+size_t tc2_const_bytes();
+size_t tc2_template_bytes(int M);
+cudaError_t launch_tc2_constants(unsigned char *cst, cudaStream_t s);
+cudaError_t launch_tc2_pretransform(const float2 *h32, int M, int K, const double2 *w64, int eH, unsigned char *H16,
+                                    cudaStream_t s);
+cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &a, const unsigned char *H16,
+                           const unsigned char *cst, int eH, int nseg, cudaStream_t s);
 
 // Time-domain form (Eq. 1 term by term) over the raw templates h [M][K].
 cudaError_t launch_td_direct(const float2 *x, int64_t n, const float2 *h, int M, int K, float *out, cudaStream_t s);

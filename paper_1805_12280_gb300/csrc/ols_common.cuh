@@ -9,13 +9,19 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
+// Barrier between the passes of a transform: the whole block by default; kernels whose
+// transform runs in one warp group pass a named-barrier policy.
+struct BlockSync {
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
 // Forward L-point FFT of the segment in `src` (natural order; e1 or another buffer) by the
 // NT = L/16 threads of a block: passes A and B exchange through e2 and e1, pass C leaves the
 // spectrum in X ("C distribution": slot g*R + k3 of thread t holds X[k1 + 16 k2 + 16 Q k3]
 // with k1 = t % 16, k2 = t / 16 + (NT/16) g).  `after_a` runs in every thread after the
 // barrier that follows pass A, when no thread reads `src` any more.  Ends before the barrier
 // that must follow it.
-template <int L, class Hook = NoHook>
+template <int L, class Hook = NoHook, class Sync = BlockSync>
 __device__ __forceinline__ void forward_fft(const float2 *src, float2 *e1, float2 *e2, const float2 *__restrict__ tw,
                                             float2 (&v)[16], float2 (&X)[16], Hook after_a = Hook())
 {
@@ -31,7 +37,7 @@ __device__ __forceinline__ void forward_fft(const float2 *src, float2 *e1, float
     for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(&tw[(tid * k) & MASK]));
 #pragma unroll
     for (int k = 0; k < 16; ++k) e2[tid + LD2 * k] = v[k];
-    __syncthreads();
+    Sync::sync();
     after_a();
     // ---- forward pass B: Q-point DFT over b, twiddle W_{QR}^{c k2}
 #pragma unroll
@@ -66,7 +72,7 @@ __device__ __forceinline__ void forward_fft(const float2 *src, float2 *e1, float
             }
         }
     }
-    __syncthreads();
+    Sync::sync();
     // ---- forward pass C: R-point DFT over c; spectrum stays in registers
     if constexpr (GC == 2) {
         const float4 *e1q = reinterpret_cast<const float4 *>(e1);

@@ -1,0 +1,715 @@
+// Two-stage tensor-core form of the overlap-save segment kernel (L = 2048): the whole inverse
+// FFT of every (segment, template) pair is two DFT-matrix GEMMs on the 5th-generation tensor
+// cores (Algorithm 2's per-filter IFFT, the M L C log2 L term of Table 1).
+//
+// Index split (Cooley-Tukey, L = 32 x 64): frequency k = k2 + 64 k1, output n = n1 + 32 n2,
+//   y[n] = sum_k2 W64^{n2 k2} [ W2048^{n1 k2} ( sum_k1 W32^{n1 k1} Y[k2 + 64 k1] ) ],
+// with W_N^e = exp(+2 pi i e / N) and Y = X . H_z (Eq. 1 through the convolution theorem).
+//
+//   stage 1  D1[(k2, s)][(n1, re/im)] = A1 . B1: A1 = Y in fp16, one TMEM lane per (k2, segment s)
+//            written by the CUDA cores right after the product; B1 = the real 64 x 64 form of
+//            the 32-point inverse DFT in shared memory.  M 128, N 64, K 64.
+//   twiddle  Z = D1 . W2048^{n1 k2} / 32 on the CUDA cores (packed FP32x2), rounded to fp16 and
+//            written MN-major into shared memory: the stage-1 rows become stage-2 columns.
+//   stage 2  D2[(n2, re/im)][(n1, s, template)] = A2 . B2: A2 = the real 128 x 128 form of the
+//            64-point inverse DFT, loaded into TMEM once per block; B2 = Z.  M 128, N 128, K 128.
+//   power    tcgen05.ld.16x256b gives one thread re and im of the same output (rows 8 apart),
+//            |y|^2 in packed FP32x2, the discard of the first K-1 outputs, coalesced stores.
+//
+// A work item is a pair of consecutive segments and a range of template pairs; a tile is one
+// template of both segments (stage 1), a pair two tiles (stage 2).  Roles: warps 0-3 run the
+// forward FFTs (FP32, once per segment) and the products, warps 4-7 the twiddles, warps 8-11
+// the power epilogue, warp 12 issues the TMA loads and the MMAs; mbarriers connect them.
+//
+// Range: the forward spectrum of each segment is scaled by a power of two chosen from its
+// largest component (|X| < 2^11) and the templates by one power of two per plan (|H| <= 16),
+// so the fp16 operands cannot overflow for any finite input; the powers carry the inverse
+// factor, an exact power of two.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fdas_internal.cuh"
+#include "fft_regs.cuh"
+#include "fft_split.cuh"
+#include "ols_common.cuh"
+#include "ptx.cuh"
+#include "tmem.cuh"
+
+namespace fdas {
+namespace tc2 {
+
+constexpr int L = 2048, NT = 128;
+constexpr int kThreads = 3 * NT + 32;          // product, twiddle and power groups + control warp
+constexpr int NH = 4;                          // template buffers in flight
+constexpr uint32_t H_ROW = 144;                // bytes per k2 row of a template: 32 half2 + 16 B pad
+constexpr uint32_t H_BYTES = 64 * H_ROW;       // 9216 per template
+// B1 [N 64 x K 64] fp16, K-major, no swizzle: core matrices 8 rows x 16 B, K step LBO, row-group step SBO.
+constexpr uint32_t LBO1 = 128, SBO1 = 1024, B1_BYTES = 8 * SBO1;
+// B2 [K 128 x N 128] fp16, MN-major, no swizzle: core matrices 8 K-rows x 16 B of N; the
+// descriptor's LBO is the step between K groups, SBO the step between N groups.
+constexpr uint32_t LBO2 = 2048, SBO2 = 128, B2_BYTES = 16 * LBO2;
+// Plan constants: B1 image | A2 rows (128 x 64 packed half2) | twiddles (64 k2 x 64 floats).
+constexpr uint32_t CB_B1 = 0, CB_A2 = CB_B1 + B1_BYTES, CB_TW = CB_A2 + 128 * 64 * 4;
+constexpr uint32_t CONST_BYTES = CB_TW + 64 * 64 * 4;
+// TMEM columns: A1 x 2, D1 x 2, A2, D2 x 2.
+constexpr uint32_t COL_A1 = 0, COL_D1 = 64, COL_A2 = 192, COL_D2 = 256, TMEM_COLS = 512;
+// kind::f16, D = F32, A = B = F16, M = 128; stage 1: B K-major, N = 64; stage 2: B MN-major, N = 128
+constexpr uint32_t IDESC1 = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t IDESC2 = (1u << 4) | (1u << 16) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+// mbarriers
+enum : int {
+    B_SEG_FULL = 0, B_SEG_FREE, B_B1_FULL,
+    B_SCALE0, B_SCALE1, B_SFREE0, B_SFREE1,   // per-item power factors: written / read
+    B_H_FULL, B_H_FREE = B_H_FULL + NH,
+    B_A1_FULL = B_H_FREE + NH, B_MMA1 = B_A1_FULL + 2, B_D1_FREE = B_MMA1 + 2,
+    B_B2_FULL = B_D1_FREE + 2, B_MMA2 = B_B2_FULL + 2, B_D2_FREE = B_MMA2 + 2,
+    B_COUNT = B_D2_FREE + 2
+};
+
+struct Smem {
+    static constexpr size_t seg = 0;                                  // 2 segments (TMA) / spectra
+    static constexpr size_t e2 = seg + 2 * sizeof(float2) * L;         // forward-FFT exchange
+    static constexpr size_t hb = e2 + sizeof(float2) * 16 * (NT + 1);  // NH template buffers
+    static constexpr size_t b1 = hb + NH * H_BYTES;
+    static constexpr size_t b2 = b1 + B1_BYTES;                       // 2 stage-2 operand buffers
+    static constexpr size_t red = b2 + 2 * B2_BYTES;                  // per-warp maxima [4][2]
+    static constexpr size_t scale = red + 8 * sizeof(float);          // [2 items][2 segments]
+    static constexpr size_t bar = scale + 4 * sizeof(float);
+    static constexpr size_t misc = bar + B_COUNT * 8;                 // TMEM address, abort flag
+    static constexpr size_t total = 1024 + misc + 16;
+    static_assert(e2 % 128 == 0 && hb % 128 == 0 && b1 % 128 == 0 && b2 % 128 == 0, "alignment");
+    static_assert(bar % 8 == 0, "mbarrier alignment");
+};
+
+struct Args {
+    const unsigned char *H16;   // [M even][64][36] half2 per template, times 2^eH
+    const unsigned char *cst;   // plan constants (CONST_BYTES)
+    const float2 *tw;           // [L] W_L^e = exp(-2 pi i e / L), FP32 (forward FFT)
+    float *out;                 // [M][n]
+    int64_t n;
+    int M, S, K;                // templates, segment step, frame length
+    int seg_begin, nseg;        // segments [seg_begin, seg_begin + nseg) of this launch
+    int n_sp, ng, ZP;           // segment pairs, template-pair groups per pair, template pairs
+    int eH;                     // template scale exponent
+    int *status;
+};
+
+__host__ __device__ inline uint32_t b1_off(int j, int k)
+{
+    return (uint32_t)((j >> 3) * SBO1 + (k >> 3) * LBO1 + (j & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// D (TMEM) (+)= A (TMEM) . B (shared-memory descriptor)
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Named barrier of the product group (warps 0-3).
+struct PSync {
+    static __device__ __forceinline__ void sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+};
+// All 128 threads of the product group agree on `ok` (and synchronise).
+__device__ __forceinline__ bool p_all(bool ok)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)ok)
+                 : "memory");
+    return r != 0;
+}
+
+// Bounded wait that also returns early once another role has given up (abort flag set).
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
+{
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// 16x256b TMEM load, 8 repetitions along the columns: 32 registers.  Thread t receives, per
+// repetition j, lane (base + t/4) columns 8j + 2(t%4) + {0, 1} in r[4j], r[4j+1] and lane
+// (base + 8 + t/4), the same columns, in r[4j+2], r[4j+3].
+__device__ __forceinline__ void tmem_ld_16x256_x8(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : FDAS_W32(r)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : FDAS_RW32(r)::"memory");
+}
+
+// ---------------------------------------------------------------------------------------
+// Plan-time kernels (FP64).
+// ---------------------------------------------------------------------------------------
+
+// exp(+2 pi i num / den) for an exact integer numerator (reduced mod den first).
+__device__ inline double2 expi(int64_t num, int den)
+{
+    const int64_t r = ((num % den) + den) % den;
+    double s, c;
+    sincospi(2.0 * (double)r / (double)den, &s, &c);
+    return make_double2(c, s);
+}
+
+// B1, A2 and the twiddle table, one thread per entry.
+__global__ void tc2_constants_kernel(unsigned char *cst)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < 64 * 64) {   // B1[j][k]: j = 4q + 2ro + e (output n1 = 2q + e, part ro), k = 2 k1 + ri
+        const int j = id / 64, k = id % 64;
+        const int n1 = 2 * (j / 4) + (j & 1), ro = (j / 2) & 1, k1 = k / 2, ri = k & 1;
+        const double2 w = expi((int64_t)n1 * k1, 32);
+        const double v = ro == 0 ? (ri == 0 ? w.x : -w.y) : (ri == 0 ? w.y : w.x);
+        reinterpret_cast<__half *>(cst + CB_B1)[b1_off(j, k) / 2] = __double2half(v);
+    } else if (id < 64 * 64 + 128 * 128) {   // A2[r][kappa]: r = 16b + 8ro + jj (n2 = 8b + jj), kappa = 64 ri + k2
+        const int e = id - 64 * 64, r = e / 128, kap = e % 128;
+        const int n2 = 8 * (r / 16) + (r & 7), ro = (r / 8) & 1, ri = kap / 64, k2 = kap % 64;
+        const double2 w = expi((int64_t)n2 * k2, 64);
+        const double v = ro == 0 ? (ri == 0 ? w.x : -w.y) : (ri == 0 ? w.y : w.x);
+        reinterpret_cast<__half *>(cst + CB_A2)[r * 128 + kap] = __double2half(v);   // column kap/2, half kap%2
+    } else if (id < 64 * 64 + 128 * 128 + 64 * 32) {   // T[k2][n1] = exp(+2 pi i n1 k2 / 2048) / 32
+        const int e = id - 64 * 64 - 128 * 128, k2 = e / 32, n1 = e % 32;
+        const double2 w = expi((int64_t)n1 * k2, L);
+        float *t = reinterpret_cast<float *>(cst + CB_TW) + k2 * 64 + 4 * (n1 / 2) + (n1 & 1);
+        t[0] = (float)(w.x / 32.0);
+        t[2] = (float)(w.y / 32.0);
+    }
+}
+
+// H16[z][k2][k1] = FFT_L(h_z)[k2 + 64 k1] * 2^eH in fp16 (direct FP64 DFT of the zero-padded
+// template, exact argument reduction), k1 = 32..35 zero padding; templates z >= M are zero.
+__global__ void tc2_pretransform_kernel(const float2 *__restrict__ h32, int M, int K, const double2 *__restrict__ w64,
+                                        int eH, int M_even, unsigned char *__restrict__ H16)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M_even * 64 * 36) return;
+    const int k1 = (int)(id % 36), k2 = (int)((id / 36) % 64), z = (int)(id / (36 * 64));
+    double re = 0.0, im = 0.0;
+    if (z < M && k1 < 32) {
+        const int f = k2 + 64 * k1;
+        const float2 *h = h32 + (size_t)z * K;
+        for (int k = 0; k < K; ++k) {
+            const double2 w = w64[((int64_t)k * f) & (L - 1)];
+            const double hr = (double)h[k].x, hi = (double)h[k].y;
+            re += hr * w.x - hi * w.y;
+            im += hr * w.y + hi * w.x;
+        }
+        re = ldexp(re, eH);
+        im = ldexp(im, eH);
+    }
+    __half2 *dst = reinterpret_cast<__half2 *>(H16 + (size_t)z * H_BYTES + (size_t)k2 * H_ROW) + k1;
+    *dst = __halves2half2(__double2half(re), __double2half(im));
+}
+
+}  // namespace tc2
+
+// ---------------------------------------------------------------------------------------
+// The segment kernel: one block per SM, work items (segment pair, template-pair range) taken
+// round-robin by block index.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(tc2::kThreads, 1)
+    ols_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const tc2::Args a)
+{
+    using namespace tc2;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float2 *segb = reinterpret_cast<float2 *>(sm + Smem::seg);
+    float2 *e2 = reinterpret_cast<float2 *>(sm + Smem::e2);
+    unsigned char *hb = sm + Smem::hb;
+    unsigned char *b2 = sm + Smem::b2;
+    float *red = reinterpret_cast<float *>(sm + Smem::red);
+    float *scl = reinterpret_cast<float *>(sm + Smem::scale);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Smem::bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Smem::misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Smem::misc + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_items = a.n_sp * a.ng;
+    constexpr int CTRL = 3 * NT;   // thread that issues copies and MMAs
+
+    if (tid == CTRL) {
+        mbar_init(&bar[B_SEG_FULL], 1);
+        mbar_init(&bar[B_SEG_FREE], NT);
+        mbar_init(&bar[B_B1_FULL], 1);
+        mbar_init(&bar[B_SCALE0], 1);
+        mbar_init(&bar[B_SCALE1], 1);
+        mbar_init(&bar[B_SFREE0], 4);   // lane 0 of each power warp
+        mbar_init(&bar[B_SFREE1], 4);
+        for (int i = 0; i < NH; ++i) {
+            mbar_init(&bar[B_H_FULL + i], 1);
+            mbar_init(&bar[B_H_FREE + i], NT);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[B_A1_FULL + i], NT);
+            mbar_init(&bar[B_MMA1 + i], 1);
+            mbar_init(&bar[B_D1_FREE + i], NT);
+            mbar_init(&bar[B_B2_FULL + i], NT);
+            mbar_init(&bar[B_MMA2 + i], 1);
+            mbar_init(&bar[B_D2_FREE + i], NT);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 12) tmem_alloc(tslot, TMEM_COLS);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    if (warp >= 8 && warp < 12) {   // stage-2 DFT matrix into TMEM: lane r holds row r
+        const int r = tid - 2 * NT;
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.cst + CB_A2 + (size_t)r * 256);
+        uint32_t v[32];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 q = __ldg(src + 8 * h + i);
+                v[4 * i] = q.x;
+                v[4 * i + 1] = q.y;
+                v[4 * i + 2] = q.z;
+                v[4 * i + 3] = q.w;
+            }
+            tmem_st32(tmem_lane_addr(tmem, COL_A2 + 32 * h), v);
+        }
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+
+    if (warp < 4) {
+        // ---------------- product group: forward FFTs, X . H_z into the stage-1 operand ----------------
+        const int k2 = tid & 63, sg = tid >> 6;
+        uint32_t t = 0;
+        int il = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
+            if (!p_all(!*abort_flag)) break;
+            const int grp = it % a.ng;
+            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+            if (!p_all(wait_bar(&bar[B_SEG_FULL], il & 1, abort_flag))) break;
+            float2 v[16], Xa[16], Xb[16];
+            forward_fft<L, NoHook, PSync>(segb, segb, e2, a.tw, v, Xa);
+            forward_fft<L, NoHook, PSync>(segb + L, segb + L, e2, a.tw, v, Xb);
+            float ma = 0.f, mb = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                ma = fmaxf(ma, fmaxf(fabsf(Xa[j].x), fabsf(Xa[j].y)));
+                mb = fmaxf(mb, fmaxf(fabsf(Xb[j].x), fabsf(Xb[j].y)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+                mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+            }
+            if (lane == 0) {
+                red[2 * warp] = ma;
+                red[2 * warp + 1] = mb;
+            }
+            PSync::sync();   // every read of the segment buffers is done; maxima visible
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int f = freq_of_slot(L, tid, j);
+                segb[f] = Xa[j];
+                segb[L + f] = Xb[j];
+            }
+            int ex[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float m = fmaxf(fmaxf(red[s], red[2 + s]), fmaxf(red[4 + s], red[6 + s]));
+                int E = 0;
+                frexpf(m, &E);
+                ex[s] = min(100, max(-60, 11 - E));   // |X| 2^e < 2^11 (|X| < 2^71)
+            }
+            if (tid == 0) {   // power factor 2^(2 (-6 - e - eH)) of each segment for the epilogue
+                if (il >= 2) wait_bar(&bar[B_SFREE0 + (il & 1)], ((il >> 1) - 1) & 1, abort_flag);
+                scl[2 * (il & 1)] = ldexpf(1.f, 2 * (-6 - ex[0] - a.eH));
+                scl[2 * (il & 1) + 1] = ldexpf(1.f, 2 * (-6 - ex[1] - a.eH));
+                mbar_arrive(&bar[B_SCALE0 + (il & 1)]);
+            }
+            PSync::sync();   // spectra in natural order visible
+            __half2 x[32], xs[32];
+            {
+                const float f = ldexpf(1.f, sg ? ex[1] : ex[0]);
+                const float2 *Xs = segb + sg * L + k2;
+#pragma unroll
+                for (int k1 = 0; k1 < 32; ++k1) {
+                    const float2 c = Xs[64 * k1];
+                    x[k1] = __floats2half2_rn(c.x * f, c.y * f);
+                    xs[k1] = __floats2half2_rn(-c.y * f, c.x * f);
+                }
+            }
+            mbar_arrive(&bar[B_SEG_FREE]);
+            for (int zp = zp0; zp < zp1; ++zp) {
+#pragma unroll 1
+                for (int zz = 0; zz < 2; ++zz, ++t) {
+                    const int slot = (int)(t % NH);
+                    wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
+                    if (t >= 2) wait_bar(&bar[B_MMA1 + (t & 1)], ((t - 2) >> 1) & 1, abort_flag);
+                    __syncwarp();
+                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
+                    tmem_fence_after_sync();
+                    const uint4 *hrow = reinterpret_cast<const uint4 *>(hb + slot * H_BYTES + k2 * H_ROW);
+                    uint32_t y[32];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint4 hv = hrow[c];
+                        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const __half2 h = *reinterpret_cast<const __half2 *>(&hw[i]);
+                            const __half2 r = __hfma2(__low2half2(h), x[4 * c + i], __hmul2(__high2half2(h), xs[4 * c + i]));
+                            y[4 * c + i] = *reinterpret_cast<const uint32_t *>(&r);
+                        }
+                    }
+                    mbar_arrive(&bar[B_H_FREE + slot]);
+                    tmem_st32(tmem_lane_addr(tmem, COL_A1 + 32 * (t & 1)), y);
+                    tmem_fence_before_sync();
+                    mbar_arrive(&bar[B_A1_FULL + (t & 1)]);
+                }
+            }
+        }
+    } else if (warp < 8) {
+        // ---------------- twiddle group: D1 . W2048^{n1 k2} / 32 -> fp16 stage-2 operand ----------------
+        const int ht = tid - NT, k2 = ht & 63, sg = ht >> 6;
+        float tw[64];
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(a.cst + CB_TW) + k2 * 16;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float4 q = __ldg(src + i);
+                tw[4 * i] = q.x;
+                tw[4 * i + 1] = q.y;
+                tw[4 * i + 2] = q.z;
+                tw[4 * i + 3] = q.w;
+            }
+        }
+        uint32_t t = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const int grp = it % a.ng;
+            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+            for (int zp = zp0; zp < zp1; ++zp) {
+#pragma unroll 1
+                for (int zz = 0; zz < 2; ++zz, ++t) {
+                    const uint32_t p = t >> 1;
+                    wait_bar(&bar[B_MMA1 + (t & 1)], (t >> 1) & 1, abort_flag);
+                    if (zz == 0 && p >= 2) wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag);
+                    __syncwarp();
+                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
+                    tmem_fence_after_sync();
+                    unsigned char *base = b2 + (p & 1) * B2_BYTES + (size_t)(4 * sg + 8 * zz) * SBO2;
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {   // n1 = 16 hh .. 16 hh + 15
+                        uint32_t d[32];
+                        tmem_ld32(tmem_lane_addr(tmem, COL_D1 + 64 * (t & 1) + 32 * hh), d);
+                        if (hh == 1) {
+                            tmem_fence_before_sync();
+                            mbar_arrive(&bar[B_D1_FREE + (t & 1)]);
+                        }
+                        uint32_t hr[8], hi[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {   // outputs n1 = 16 hh + 2q, +1
+                            const float2 re = make_float2(__uint_as_float(d[4 * q]), __uint_as_float(d[4 * q + 1]));
+                            const float2 im = make_float2(__uint_as_float(d[4 * q + 2]), __uint_as_float(d[4 * q + 3]));
+                            const int w = 4 * (8 * hh + q);
+                            const float2 tr = make_float2(tw[w], tw[w + 1]), ti = make_float2(tw[w + 2], tw[w + 3]);
+                            const float2 zr = csub(pmul(re, tr), pmul(im, ti));
+                            const float2 zi = pfma(re, ti, pmul(im, tr));
+                            hr[q] = pack_h2(zr.x, zr.y);
+                            hi[q] = pack_h2(zi.x, zi.y);
+                        }
+#pragma unroll
+                        for (int ri = 0; ri < 2; ++ri) {
+                            const int kap = 64 * ri + k2;
+                            unsigned char *row = base + (kap >> 3) * LBO2 + (kap & 7) * 16;
+                            const uint32_t *hv = ri ? hi : hr;
+#pragma unroll
+                            for (int c = 0; c < 2; ++c)   // n1 group of 8: 2 hh + c
+                                *reinterpret_cast<uint4 *>(row + (2 * hh + c) * SBO2) =
+                                    make_uint4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
+                        }
+                    }
+                    if (zz == 1) {
+                        fence_proxy_async_smem();
+                        mbar_arrive(&bar[B_B2_FULL + (p & 1)]);
+                    }
+                }
+            }
+        }
+    } else if (warp < 12) {
+        // ---------------- power group: |D2|^2 x 2^(2f), discard, stores ----------------
+        const int q = warp & 3;
+        uint32_t p = 0;
+        int il = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
+            const int sp = it / a.ng, grp = it % a.ng;
+            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+            wait_bar(&bar[B_SCALE0 + (il & 1)], (il >> 1) & 1, abort_flag);
+            float fsc[2] = {scl[2 * (il & 1)], scl[2 * (il & 1) + 1]};
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_SFREE0 + (il & 1)]);
+            int64_t segrow[2];
+            bool segok[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                segok[s] = 2 * sp + s < a.nseg;
+                segrow[s] = (int64_t)(a.seg_begin + 2 * sp + s) * a.S;
+            }
+            for (int zp = zp0; zp < zp1; ++zp, ++p) {
+                wait_bar(&bar[B_MMA2 + (p & 1)], (p >> 1) & 1, abort_flag);
+                __syncwarp();
+                if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
+                tmem_fence_after_sync();
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    const int n2 = 8 * (2 * q + h) + (lane >> 2);
+                    const int tbase = 2 * (lane & 3) + 32 * n2 - (a.K - 1);
+#pragma unroll 1
+                    for (int c = 0; c < 2; ++c) {
+                        uint32_t r[32];
+                        tmem_ld_16x256_x8(tmem + ((uint32_t)(32 * q + 16 * h) << 16) + COL_D2 + 128 * (p & 1) + 64 * c, r);
+                        if (h == 1 && c == 1) {
+                            tmem_fence_before_sync();
+                            mbar_arrive(&bar[B_D2_FREE + (p & 1)]);
+                        }
+                        const int z = 2 * zp + c;
+                        if (z >= a.M) continue;
+                        float *rowp = a.out + (size_t)z * (size_t)a.n;
+                        const bool al8 = (reinterpret_cast<uintptr_t>(rowp) & 7) == 0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int s = j >> 2;
+                            const int tout = tbase + 8 * (j & 3);
+                            const int64_t idx = segrow[s] + tout;
+                            if (!segok[s] || tout < 0 || tout >= a.S || idx >= a.n) continue;
+                            const float2 re = make_float2(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]));
+                            const float2 im = make_float2(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                            const float2 pw = pmul(pfma(re, re, pmul(im, im)), make_float2(fsc[s], fsc[s]));
+                            if (idx + 1 < a.n) {
+                                if (al8) *reinterpret_cast<float2 *>(rowp + idx) = pw;
+                                else {
+                                    rowp[idx] = pw.x;
+                                    rowp[idx + 1] = pw.y;
+                                }
+                            } else {
+                                rowp[idx] = pw.x;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- control thread: TMA loads and MMAs ----------------
+        const uint32_t b1a = smem_u32(sm + Smem::b1), b2a = smem_u32(b2);
+        mbar_arrive_expect_tx(&bar[B_B1_FULL], B1_BYTES);
+        bulk_load(sm + Smem::b1, a.cst + CB_B1, B1_BYTES, &bar[B_B1_FULL]);
+        uint32_t seg_issued = 0;
+        auto issue_segments = [&](int it) {
+            const int sp = it / a.ng;
+            mbar_arrive_expect_tx(&bar[B_SEG_FULL], 2u * L * (uint32_t)sizeof(float2));
+#pragma unroll 1
+            for (int s = 0; s < 2; ++s) {
+                const int c0 = (a.seg_begin + 2 * sp + s) * a.S - (a.K - 1);
+#pragma unroll
+                for (int j = 0; j < L / 256; ++j) tma_load_1d(segb + s * L + 256 * j, &tmap, c0 + 256 * j, &bar[B_SEG_FULL]);
+            }
+            ++seg_issued;
+        };
+        if ((int)blockIdx.x < n_items) issue_segments(blockIdx.x);
+        bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
+        // template-load cursor, NH tiles ahead of the MMAs
+        int h_it = blockIdx.x, h_zp = 0, h_zz = 0;
+        if (h_it < n_items) h_zp = a.ZP * (h_it % a.ng) / a.ng;
+        uint32_t tH = 0, t = 0, p1 = 0, p2 = 0;
+        auto issue_mma2 = [&]() {
+            const uint32_t q = p2;
+            ok = ok && wait_bar(&bar[B_B2_FULL + (q & 1)], (q >> 1) & 1, abort_flag);
+            if (q >= 2) ok = ok && wait_bar(&bar[B_D2_FREE + (q & 1)], ((q - 2) >> 1) & 1, abort_flag);
+            if (!ok) return;
+            tmem_fence_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks)
+                mma_ts(tmem + COL_D2 + 128 * (q & 1), tmem + COL_A2 + 8 * ks,
+                       smem_desc(b2a + (q & 1) * B2_BYTES + ks * 2 * LBO2, LBO2, SBO2), IDESC2, ks > 0);
+            mma_commit(&bar[B_MMA2 + (q & 1)]);
+            ++p2;
+        };
+        int il = 0;
+        for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x, ++il) {
+            const int grp = it % a.ng;
+            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+            for (int zp = zp0; ok && zp < zp1; ++zp) {
+                for (int zz = 0; ok && zz < 2; ++zz) {
+                    while (tH < t + NH && h_it < n_items) {   // template loads ahead
+                        const uint32_t slot = tH % NH;
+                        if (tH >= NH) ok = ok && wait_bar(&bar[B_H_FREE + slot], ((tH / NH) - 1) & 1, abort_flag);
+                        if (!ok) break;
+                        mbar_arrive_expect_tx(&bar[B_H_FULL + slot], H_BYTES);
+                        bulk_load(hb + slot * H_BYTES, a.H16 + (size_t)(2 * h_zp + h_zz) * H_BYTES, H_BYTES,
+                                  &bar[B_H_FULL + slot]);
+                        ++tH;
+                        if (++h_zz == 2) {
+                            h_zz = 0;
+                            if (++h_zp >= a.ZP * (h_it % a.ng + 1) / a.ng) {
+                                h_it += gridDim.x;
+                                if (h_it < n_items) h_zp = a.ZP * (h_it % a.ng) / a.ng;
+                            }
+                        }
+                    }
+                    ok = ok && wait_bar(&bar[B_A1_FULL + (t & 1)], (t >> 1) & 1, abort_flag);
+                    if (t >= 2) ok = ok && wait_bar(&bar[B_D1_FREE + (t & 1)], ((t - 2) >> 1) & 1, abort_flag);
+                    if (!ok) break;
+                    tmem_fence_after_sync();
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        mma_ts(tmem + COL_D1 + 64 * (t & 1), tmem + COL_A1 + 32 * (t & 1) + 8 * ks,
+                               smem_desc(b1a + ks * 2 * LBO1, LBO1, SBO1), IDESC1, ks > 0);
+                    mma_commit(&bar[B_MMA1 + (t & 1)]);
+                    ++t;
+                    // the product group has taken this item's spectra: load the next item's segments
+                    if (zp == zp0 && zz == 0 && it + (int)gridDim.x < n_items) {
+                        ok = ok && wait_bar(&bar[B_SEG_FREE], il & 1, abort_flag);
+                        if (ok) issue_segments(it + gridDim.x);
+                    }
+                }
+                if (!ok) break;
+                ++p1;
+                if (p1 - p2 >= 2) issue_mma2();
+            }
+        }
+        while (ok && p2 < p1) issue_mma2();
+        // nothing may be in flight when the block leaves: copies and MMAs issued land first
+        if (seg_issued) mbar_wait_bounded(&bar[B_SEG_FULL], (seg_issued - 1) & 1, kWaitLimitNs);
+        for (uint32_t i = (tH > NH ? tH - NH : 0); i < tH; ++i)
+            mbar_wait_bounded(&bar[B_H_FULL + i % NH], (i / NH) & 1, kWaitLimitNs);
+        for (uint32_t i = (t > 2 ? t - 2 : 0); i < t; ++i) mbar_wait_bounded(&bar[B_MMA1 + (i & 1)], (i >> 1) & 1, kWaitLimitNs);
+        for (uint32_t i = (p2 > 2 ? p2 - 2 : 0); i < p2; ++i)
+            mbar_wait_bounded(&bar[B_MMA2 + (i & 1)], (i >> 1) & 1, kWaitLimitNs);
+        if (!ok || *abort_flag) {
+            *abort_flag = 1;
+            atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+        }
+    }
+    __syncwarp();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 12) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------------------
+size_t tc2_const_bytes() { return tc2::CONST_BYTES; }
+size_t tc2_template_bytes(int M) { return (size_t)(2 * ((M + 1) / 2)) * tc2::H_BYTES; }
+
+cudaError_t launch_tc2_constants(unsigned char *cst, cudaStream_t s)
+{
+    const int total = 64 * 64 + 128 * 128 + 64 * 32;
+    tc2::tc2_constants_kernel<<<(total + 255) / 256, 256, 0, s>>>(cst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc2_pretransform(const float2 *h32, int M, int K, const double2 *w64, int eH, unsigned char *H16,
+                                    cudaStream_t s)
+{
+    const int M_even = 2 * ((M + 1) / 2);
+    const int64_t total = (int64_t)M_even * 64 * 36;
+    tc2::tc2_pretransform_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h32, M, K, w64, eH, M_even, H16);
+    return cudaGetLastError();
+}
+
+// Template-pair groups per segment pair: the fewest waves of (one block per SM) x the items'
+// length in template pairs plus about two pairs of fixed cost (the two forward FFTs and the
+// pipeline fill and drain).
+static int tc2_groups(int64_t n_sp, int ZP, int sms)
+{
+    int best_ng = 1;
+    double best = 1e300;
+    for (int ng = 1; ng <= ZP && ng <= 64; ++ng) {
+        const int64_t items = n_sp * ng;
+        const int64_t waves = (items + sms - 1) / sms;
+        const double cost = (double)waves * ((double)((ZP + ng - 1) / ng) + 2.0);
+        if (cost < best * (1.0 - 1e-9)) {
+            best = cost;
+            best_ng = ng;
+        }
+    }
+    return best_ng;
+}
+
+cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsigned char *H16,
+                           const unsigned char *cst, int eH, int nseg, cudaStream_t s)
+{
+    static bool done[64] = {};
+    static int sms[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(ols_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    if (nseg <= 0) return cudaSuccess;
+    tc2::Args a;
+    a.H16 = H16;
+    a.cst = cst;
+    a.tw = o.tw;
+    a.out = o.out;
+    a.n = o.n;
+    a.M = o.M;
+    a.S = o.S;
+    a.K = o.K;
+    a.seg_begin = o.seg_begin;
+    a.nseg = nseg;
+    a.n_sp = (nseg + 1) / 2;
+    a.ZP = (o.M + 1) / 2;
+    a.ng = tc2_groups(a.n_sp, a.ZP, sms[dev]);
+    a.eH = eH;
+    a.status = o.status;
+    const int64_t items = (int64_t)a.n_sp * a.ng;
+    const int grid = (int)(items < sms[dev] ? items : sms[dev]);
+    ols_tc2_kernel<<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a);
+    return cudaGetLastError();
+}
+
+}  // namespace fdas

@@ -26,6 +26,7 @@ FDAS_ERR_UNSUPPORTED = -7
 
 FDAS_PREC_FP32 = 0
 FDAS_PREC_TC_FP16 = 1
+FDAS_PREC_TC_DFT2 = 2
 
 
 class FdasError(RuntimeError):

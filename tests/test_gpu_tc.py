@@ -1,9 +1,11 @@
-"""GPU parity of the tensor-core form (fp16 DFT-GEMM radix-16 passes) against the FP64 oracle."""
+"""GPU parity of the tensor-core forms against the FP64 oracle: the radix-16 DFT-GEMM pass
+(FDAS_PREC_TC_FP16) and the two-stage form that takes the whole inverse FFT
+(FDAS_PREC_TC_DFT2)."""
 import numpy as np
 import pytest
 
 import synth
-from parity import TOL_TC, compare
+from parity import THRESHOLD_GAUSS, TOL_TC, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -24,16 +26,21 @@ def bank():
     return synth.template_bank()[0]
 
 
+@pytest.fixture(scope="module", params=["tc_fp16", "tc_dft2"])
+def prec(request, fd):
+    return {"tc_fp16": fd.FDAS_PREC_TC_FP16, "tc_dft2": fd.FDAS_PREC_TC_DFT2}[request.param]
+
+
 def _run(plan, x):
     out = plan.convolve(torch.from_numpy(np.ascontiguousarray(x)).cuda())
     plan.status()
     return out.cpu().numpy()
 
 
-def test_small_array_vs_direct(fd, oracle_mod, bank):
+def test_small_array_vs_direct(fd, oracle_mod, bank, prec):
     x = synth.make_input(synth.single_small())
-    with fd.Plan(bank, n_max=x.size, precision=fd.FDAS_PREC_TC_FP16) as plan:
-        assert plan.desc.precision == fd.FDAS_PREC_TC_FP16
+    with fd.Plan(bank, n_max=x.size, precision=prec) as plan:
+        assert plan.desc.precision == prec
         p = _run(plan, x)
     info = compare(p, oracle_mod.direct_power(x, bank), TOL_TC)
     # two fp16 roundings of the data (relative 2^-12 RMS each) bound the relative RMS error
@@ -46,42 +53,60 @@ def test_small_array_vs_direct(fd, oracle_mod, bank):
 
 @pytest.mark.parametrize("n", [1, 7, 1627, 1628, 1629, 2048, 5000, 9001])
 @pytest.mark.parametrize("G", [1, 7, 85])
-def test_ragged_and_groups(fd, oracle_mod, bank, n, G):
+def test_ragged_and_groups(fd, oracle_mod, bank, prec, n, G):
     rng = np.random.default_rng(n * 3 + G)
     x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     hs = bank[::4] if G != 85 else bank
-    with fd.Plan(hs, n_max=max(n, 16), tpl_per_cta=min(G, hs.shape[0]), precision=fd.FDAS_PREC_TC_FP16) as plan:
+    with fd.Plan(hs, n_max=max(n, 16), tpl_per_cta=min(G, hs.shape[0]), precision=prec) as plan:
         p = _run(plan, x)
     # fp16 data round relative to the segment's energy, which includes the outputs past n
-    # that overlap-save computes and discards: for arrays shorter than a template the
-    # tolerance is taken against the maximum of the untruncated convolution
-    full = oracle_mod.direct_power(np.concatenate([x, np.zeros(hs.shape[1] - 1, np.complex64)]), hs)
-    compare(p, oracle_mod.direct_power(x, hs), TOL_TC, scale=max(float(full.max()), 0.0))
+    # that overlap-save computes and discards: only for arrays shorter than a template
+    # (n < K, where the kept outputs are a small part of that energy) is the tolerance taken
+    # against the maximum of the untruncated convolution; otherwise against max(P_ref)
+    ref = oracle_mod.direct_power(x, hs)
+    scale = None
+    if n < hs.shape[1]:
+        full = oracle_mod.direct_power(np.concatenate([x, np.zeros(hs.shape[1] - 1, np.complex64)]), hs)
+        scale = float(full.max())
+    compare(p, ref, TOL_TC, scale=scale)
+
+
+@pytest.mark.parametrize("log2n", [18, 20])
+def test_noise_candidates_elementwise(fd, oracle_mod, bank, prec, log2n):
+    # noise only: max(P_ref) is about ln(85 N), so 2e-3 max(P_ref) is far below T = 7 and the
+    # candidate rule is tested cell by cell (the band around T holds a handful of points)
+    x = synth.make_input(synth.ArraySpec(n=1 << log2n, seed=40 + log2n))
+    with fd.Plan(bank, n_max=x.size, precision=prec) as plan:
+        p = _run(plan, x)
+    ref = oracle_mod.ols_power(x, bank, L=2048)
+    info = compare(p, ref, TOL_TC)
+    assert TOL_TC * info["scale"] < 7.0 and info["candidates"] > 1000, info
+    compare(p, ref, TOL_TC, threshold=THRESHOLD_GAUSS)
 
 
 @pytest.mark.parametrize("k", [1, 2, 64, 421, 1000, 2044])
-def test_template_lengths(fd, oracle_mod, k):
+def test_template_lengths(fd, oracle_mod, prec, k):
     rng = np.random.default_rng(k + 7)
     n = 6000
     x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     h = ((rng.standard_normal((3, k)) + 1j * rng.standard_normal((3, k))) / np.sqrt(2 * k)).astype(np.complex64)
-    with fd.Plan(h, n_max=n, precision=fd.FDAS_PREC_TC_FP16) as plan:
+    with fd.Plan(h, n_max=n, precision=prec) as plan:
         p = _run(plan, x)
     compare(p, oracle_mod.direct_power(x, h), TOL_TC)
 
 
-def test_unsupported_options(fd, bank):
+def test_unsupported_options(fd, bank, prec):
     for kw in (dict(seg_len=1024), dict(seg_len=4096), dict(autotune=1)):
         with pytest.raises(fd.FdasError) as e:
-            fd.Plan(bank, n_max=1000, precision=fd.FDAS_PREC_TC_FP16, **kw)
+            fd.Plan(bank, n_max=1000, precision=prec, **kw)
         assert e.value.code == fd.fdas.FDAS_ERR_UNSUPPORTED
 
 
 @pytest.mark.slow
-def test_ska_array_vs_ols_oracle(fd, oracle_mod, bank):
+def test_ska_array_vs_ols_oracle(fd, oracle_mod, bank, prec):
     spec = synth.single_ska()
     x = synth.make_input(spec)
-    with fd.Plan(bank, n_max=x.size, precision=fd.FDAS_PREC_TC_FP16) as plan:
+    with fd.Plan(bank, n_max=x.size, precision=prec) as plan:
         out = plan.convolve(torch.from_numpy(x).cuda())
         plan.status()
         p = out.cpu().numpy()
@@ -93,3 +118,59 @@ def test_ska_array_vs_ols_oracle(fd, oracle_mod, bank):
         m = 42 + int(c.z)
         i = int(round(c.r + c.z / 2)) + 210
         assert p[m, i - 3:i + 4].max() > 20 * np.median(p[m])
+
+
+def test_batched_forms_reject_tensor_core_plans(fd, bank, prec):
+    # the batched, allocation-free and served entry points run the FP32 persistent kernel:
+    # a tensor-core plan is refused before anything is enqueued (the outputs keep their sentinel)
+    n = 5000
+    x = torch.from_numpy((np.arange(n) % 7 - 3).astype(np.complex64)).cuda()
+    out = torch.full((bank.shape[0], n), -1.0, dtype=torch.float32, device="cuda")
+    with fd.Plan(bank, n_max=n, precision=prec) as plan:
+        for call in (fd.fdas_convolve_batch, fd.fdas_convolve_batch_noalloc):
+            with pytest.raises(fd.FdasError) as e:
+                call(plan.handle, [x.data_ptr()], [n], [out.data_ptr()])
+            assert e.value.code == fd.fdas.FDAS_ERR_UNSUPPORTED
+        with pytest.raises(fd.FdasError) as e:
+            fd.fdas_server_create(plan.handle, 1 << 28)
+        assert e.value.code == fd.fdas.FDAS_ERR_UNSUPPORTED
+        torch.cuda.synchronize()
+    assert bool((out == -1.0).all())
+
+
+@pytest.mark.parametrize("gain", [1e-9, 1e-3, 1.0, 1e4])
+def test_dft2_input_scale(fd, oracle_mod, bank, gain):
+    # the two-stage form scales each segment's spectrum by a power of two before the fp16
+    # operands: the relative error does not depend on the input's magnitude
+    x = (synth.make_input(synth.single_small(n=9000, seed=3)) * np.float32(gain)).astype(np.complex64)
+    with fd.Plan(bank, n_max=x.size, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        p = _run(plan, x)
+    ref = oracle_mod.direct_power(x, bank)
+    info = compare(p, ref, TOL_TC, threshold=7.0 * gain * gain)
+    assert info["rel"] < 1e-3, info
+
+
+def test_dft2_zero_and_host_path(fd, oracle_mod, bank):
+    # an all-zero array gives an all-zero plane; the host-buffer path (chunked launches over
+    # segment ranges) gives the same bits as the device path
+    with fd.Plan(bank, n_max=40000, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        z = _run(plan, np.zeros(5000, np.complex64))
+        assert not np.any(z)
+        x = synth.make_input(synth.single_small(n=40000, seed=9))
+        dev = _run(plan, x)
+        host = plan.convolve_host(x)
+    assert np.array_equal(dev, host)
+    compare(dev, oracle_mod.ols_power(x, bank, L=2048), TOL_TC)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 85, 130])
+def test_dft2_template_counts(fd, oracle_mod, m):
+    # odd counts leave the second template of the last pair empty; more templates than the
+    # synthetic bank use random unit-energy taps
+    rng = np.random.default_rng(m)
+    n, k = 7000, 200
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    h = ((rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))) / np.sqrt(2 * k)).astype(np.complex64)
+    with fd.Plan(h, n_max=n, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        p = _run(plan, x)
+    compare(p, oracle_mod.direct_power(x, h), TOL_TC)
