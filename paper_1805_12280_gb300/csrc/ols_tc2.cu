@@ -11,15 +11,18 @@
 //            the 32-point inverse DFT in shared memory.  M 128, N 64, K 64.
 //   twiddle  Z = D1 . W2048^{n1 k2} / 32 on the CUDA cores (packed FP32x2), rounded to fp16 and
 //            written MN-major into shared memory: the stage-1 rows become stage-2 columns.
-//   stage 2  D2[(n2, re/im)][(n1, s, template)] = A2 . B2: A2 = the real 128 x 128 form of the
-//            64-point inverse DFT, loaded into TMEM once per block; B2 = Z.  M 128, N 128, K 128.
-//   power    tcgen05.ld.16x256b gives one thread re and im of the same output (rows 8 apart),
-//            |y|^2 in packed FP32x2, the discard of the first K-1 outputs, coalesced stores.
+//   stage 2  D2[(n1, s, template)][(n2, re/im)] = Z . G: Z in shared memory (MN-major A operand),
+//            G = the real 128 x 128 form of the 64-point inverse DFT (K-major B operand, loaded
+//            once per block).  M 128, N 128, K 128: two templates of two segments per MMA.
+//   power    one TMEM lane per (n1, segment, template) holds re and im of its 64 outputs
+//            n1 + 32 n2: |y|^2 in packed FP32x2, the discard of the first K-1 outputs, and stores
+//            in which a warp writes 32 consecutive outputs (128 contiguous bytes).
 //
 // A work item is a pair of consecutive segments and a range of template pairs; a tile is one
 // template of both segments (stage 1), a pair two tiles (stage 2).  Roles: warps 0-3 run the
 // forward FFTs (FP32, once per segment) and the products, warps 4-7 the twiddles, warps 8-11
-// the power epilogue, warp 12 issues the TMA loads and the MMAs; mbarriers connect them.
+// the power epilogue, warps 12 and 14 issue the stage-1 and stage-2 MMAs, warp 13 the TMA loads;
+// mbarriers connect them.
 //
 // Range: the forward spectrum of each segment is scaled by a power of two chosen from its
 // largest component (|X| < 2^11) and the templates by one power of two per plan (|H| <= 16),
@@ -42,31 +45,35 @@ namespace fdas {
 namespace tc2 {
 
 constexpr int L = 2048, NT = 128;
-constexpr int kThreads = 3 * NT + 32;          // product, twiddle and power groups + control warp
+constexpr int kThreads = 3 * NT + 96;          // product, twiddle, power groups + 2 MMA warps + loader
 constexpr int NH = 4;                          // template buffers in flight
 constexpr uint32_t H_ROW = 144;                // bytes per k2 row of a template: 32 half2 + 16 B pad
 constexpr uint32_t H_BYTES = 64 * H_ROW;       // 9216 per template
 // B1 [N 64 x K 64] fp16, K-major, no swizzle: core matrices 8 rows x 16 B, K step LBO, row-group step SBO.
 constexpr uint32_t LBO1 = 128, SBO1 = 1024, B1_BYTES = 8 * SBO1;
-// B2 [K 128 x N 128] fp16, MN-major, no swizzle: core matrices 8 K-rows x 16 B of N; the
-// descriptor's LBO is the step between K groups, SBO the step between N groups.
+// Z [M 128 x K 128] fp16, MN-major, no swizzle: core matrices 8 K-rows x 16 B of M; the
+// descriptor's LBO is the step between K groups, SBO the step between M groups.
 constexpr uint32_t LBO2 = 2048, SBO2 = 128, B2_BYTES = 16 * LBO2;
-// Plan constants: B1 image | A2 rows (128 x 64 packed half2) | twiddles (64 k2 x 64 floats).
-constexpr uint32_t CB_B1 = 0, CB_A2 = CB_B1 + B1_BYTES, CB_TW = CB_A2 + 128 * 64 * 4;
+// G [N 128 x K 128] fp16, K-major, no swizzle.
+constexpr uint32_t LBOG = 128, SBOG = 16 * LBOG, G_BYTES = 16 * SBOG;
+// Plan constants: B1 image | G image | twiddles (64 k2 x 64 floats).
+constexpr uint32_t CB_B1 = 0, CB_G = CB_B1 + B1_BYTES, CB_TW = CB_G + G_BYTES;
 constexpr uint32_t CONST_BYTES = CB_TW + 64 * 64 * 4;
-// TMEM columns: A1 x 2, D1 x 2, A2, D2 x 2.
-constexpr uint32_t COL_A1 = 0, COL_D1 = 64, COL_A2 = 192, COL_D2 = 256, TMEM_COLS = 512;
-// kind::f16, D = F32, A = B = F16, M = 128; stage 1: B K-major, N = 64; stage 2: B MN-major, N = 128
+// TMEM columns: A1 x 2, D1 x 3, D2 x 2.
+constexpr uint32_t COL_A1 = 0, COL_D1 = 64, COL_D2 = 256, TMEM_COLS = 512;
+constexpr uint32_t ND1 = 3;                    // stage-1 accumulators in flight (A1: 2)
+// kind::f16, D = F32, A = B = F16, M = 128.  Stage 1: A from TMEM, B K-major, N = 64.
+// Stage 2: A MN-major (bit 15), B K-major, N = 128.
 constexpr uint32_t IDESC1 = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t IDESC2 = (1u << 4) | (1u << 16) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t IDESC2 = (1u << 4) | (1u << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 // mbarriers
 enum : int {
     B_SEG_FULL = 0, B_SEG_FREE, B_B1_FULL,
     B_SCALE0, B_SCALE1, B_SFREE0, B_SFREE1,   // per-item power factors: written / read
     B_H_FULL, B_H_FREE = B_H_FULL + NH,
-    B_A1_FULL = B_H_FREE + NH, B_MMA1 = B_A1_FULL + 2, B_D1_FREE = B_MMA1 + 2,
-    B_B2_FULL = B_D1_FREE + 2, B_MMA2 = B_B2_FULL + 2, B_D2_FREE = B_MMA2 + 2,
+    B_A1_FULL = B_H_FREE + NH, B_MMA1 = B_A1_FULL + 2, B_D1_FREE = B_MMA1 + ND1,
+    B_B2_FULL = B_D1_FREE + ND1, B_MMA2 = B_B2_FULL + 2, B_D2_FREE = B_MMA2 + 2,
     B_COUNT = B_D2_FREE + 2
 };
 
@@ -75,7 +82,8 @@ struct Smem {
     static constexpr size_t e2 = seg + 2 * sizeof(float2) * L;         // forward-FFT exchange
     static constexpr size_t hb = e2 + sizeof(float2) * 16 * (NT + 1);  // NH template buffers
     static constexpr size_t b1 = hb + NH * H_BYTES;
-    static constexpr size_t b2 = b1 + B1_BYTES;                       // 2 stage-2 operand buffers
+    static constexpr size_t g = b1 + B1_BYTES;                        // stage-2 DFT matrix
+    static constexpr size_t b2 = g + G_BYTES;                         // 2 stage-2 operand buffers
     static constexpr size_t red = b2 + 2 * B2_BYTES;                  // per-warp maxima [4][2]
     static constexpr size_t scale = red + 8 * sizeof(float);          // [2 items][2 segments]
     static constexpr size_t bar = scale + 4 * sizeof(float);
@@ -102,11 +110,24 @@ __host__ __device__ inline uint32_t b1_off(int j, int k)
 {
     return (uint32_t)((j >> 3) * SBO1 + (k >> 3) * LBO1 + (j & 7) * 16 + (k & 7) * 2);
 }
+__host__ __device__ inline uint32_t g_off(int c, int k)
+{
+    return (uint32_t)((c >> 3) * SBOG + (k >> 3) * LBOG + (c & 7) * 16 + (k & 7) * 2);
+}
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// D (TMEM) (+)= A (shared-memory descriptor) . B (shared-memory descriptor)
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 // D (TMEM) (+)= A (TMEM) . B (shared-memory descriptor)
@@ -161,19 +182,6 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// 16x256b TMEM load, 8 repetitions along the columns: 32 registers.  Thread t receives, per
-// repetition j, lane (base + t/4) columns 8j + 2(t%4) + {0, 1} in r[4j], r[4j+1] and lane
-// (base + 8 + t/4), the same columns, in r[4j+2], r[4j+3].
-__device__ __forceinline__ void tmem_ld_16x256_x8(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : FDAS_W32(r)
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : FDAS_RW32(r)::"memory");
-}
-
 // ---------------------------------------------------------------------------------------
 // Plan-time kernels (FP64).
 // ---------------------------------------------------------------------------------------
@@ -187,7 +195,7 @@ __device__ inline double2 expi(int64_t num, int den)
     return make_double2(c, s);
 }
 
-// B1, A2 and the twiddle table, one thread per entry.
+// B1, G and the twiddle table, one thread per entry.
 __global__ void tc2_constants_kernel(unsigned char *cst)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,12 +205,12 @@ __global__ void tc2_constants_kernel(unsigned char *cst)
         const double2 w = expi((int64_t)n1 * k1, 32);
         const double v = ro == 0 ? (ri == 0 ? w.x : -w.y) : (ri == 0 ? w.y : w.x);
         reinterpret_cast<__half *>(cst + CB_B1)[b1_off(j, k) / 2] = __double2half(v);
-    } else if (id < 64 * 64 + 128 * 128) {   // A2[r][kappa]: r = 16b + 8ro + jj (n2 = 8b + jj), kappa = 64 ri + k2
-        const int e = id - 64 * 64, r = e / 128, kap = e % 128;
-        const int n2 = 8 * (r / 16) + (r & 7), ro = (r / 8) & 1, ri = kap / 64, k2 = kap % 64;
+    } else if (id < 64 * 64 + 128 * 128) {   // G[c][kappa]: c = 4 (n2/2) + 2 ro + n2 % 2, kappa = 64 ri + k2
+        const int e = id - 64 * 64, c = e / 128, kap = e % 128;
+        const int n2 = 2 * (c / 4) + (c & 1), ro = (c / 2) & 1, ri = kap / 64, k2 = kap % 64;
         const double2 w = expi((int64_t)n2 * k2, 64);
         const double v = ro == 0 ? (ri == 0 ? w.x : -w.y) : (ri == 0 ? w.y : w.x);
-        reinterpret_cast<__half *>(cst + CB_A2)[r * 128 + kap] = __double2half(v);   // column kap/2, half kap%2
+        reinterpret_cast<__half *>(cst + CB_G)[g_off(c, kap) / 2] = __double2half(v);
     } else if (id < 64 * 64 + 128 * 128 + 64 * 32) {   // T[k2][n1] = exp(+2 pi i n1 k2 / 2048) / 32
         const int e = id - 64 * 64 - 128 * 128, k2 = e / 32, n1 = e % 32;
         const double2 w = expi((int64_t)n1 * k2, L);
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = a.n_sp * a.ng;
-    constexpr int CTRL = 3 * NT;   // thread that issues copies and MMAs
+    constexpr int CTRL = 3 * NT;   // the MMA thread initialises the barriers
 
     if (tid == CTRL) {
         mbar_init(&bar[B_SEG_FULL], 1);
@@ -275,10 +283,12 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             mbar_init(&bar[B_H_FULL + i], 1);
             mbar_init(&bar[B_H_FREE + i], NT);
         }
+        for (int i = 0; i < (int)ND1; ++i) {
+            mbar_init(&bar[B_MMA1 + i], 1);        // stage 1 of tile t done: D1[t % 3] full, A1[t % 2] free
+            mbar_init(&bar[B_D1_FREE + i], NT);
+        }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar[B_A1_FULL + i], NT);
-            mbar_init(&bar[B_MMA1 + i], 1);
-            mbar_init(&bar[B_D1_FREE + i], NT);
             mbar_init(&bar[B_B2_FULL + i], NT);
             mbar_init(&bar[B_MMA2 + i], 1);
             mbar_init(&bar[B_D2_FREE + i], NT);
@@ -291,27 +301,6 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     __syncthreads();
     tmem_fence_after_sync();
     const uint32_t tmem = *tslot;
-
-    if (warp >= 8 && warp < 12) {   // stage-2 DFT matrix into TMEM: lane r holds row r
-        const int r = tid - 2 * NT;
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.cst + CB_A2 + (size_t)r * 256);
-        uint32_t v[32];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const uint4 q = __ldg(src + 8 * h + i);
-                v[4 * i] = q.x;
-                v[4 * i + 1] = q.y;
-                v[4 * i + 2] = q.z;
-                v[4 * i + 3] = q.w;
-            }
-            tmem_st32(tmem_lane_addr(tmem, COL_A2 + 32 * h), v);
-        }
-    }
-    tmem_fence_before_sync();
-    __syncthreads();
-    tmem_fence_after_sync();
 
     if (warp < 4) {
         // ---------------- product group: forward FFTs, X . H_z into the stage-1 operand ----------------
@@ -380,7 +369,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                 for (int zz = 0; zz < 2; ++zz, ++t) {
                     const int slot = (int)(t % NH);
                     wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
-                    if (t >= 2) wait_bar(&bar[B_MMA1 + (t & 1)], ((t - 2) >> 1) & 1, abort_flag);
+                    if (t >= 2) wait_bar(&bar[B_MMA1 + (t - 2) % ND1], ((t - 2) / ND1) & 1, abort_flag);
                     __syncwarp();
                     if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
                     tmem_fence_after_sync();
@@ -427,7 +416,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
 #pragma unroll 1
                 for (int zz = 0; zz < 2; ++zz, ++t) {
                     const uint32_t p = t >> 1;
-                    wait_bar(&bar[B_MMA1 + (t & 1)], (t >> 1) & 1, abort_flag);
+                    wait_bar(&bar[B_MMA1 + t % ND1], (t / ND1) & 1, abort_flag);
                     if (zz == 0 && p >= 2) wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag);
                     __syncwarp();
                     if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
@@ -436,10 +425,10 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {   // n1 = 16 hh .. 16 hh + 15
                         uint32_t d[32];
-                        tmem_ld32(tmem_lane_addr(tmem, COL_D1 + 64 * (t & 1) + 32 * hh), d);
+                        tmem_ld32(tmem_lane_addr(tmem, COL_D1 + 64 * (t % ND1) + 32 * hh), d);
                         if (hh == 1) {
                             tmem_fence_before_sync();
-                            mbar_arrive(&bar[B_D1_FREE + (t & 1)]);
+                            mbar_arrive(&bar[B_D1_FREE + t % ND1]);
                         }
                         uint32_t hr[8], hi[8];
 #pragma unroll
@@ -473,154 +462,150 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         }
     } else if (warp < 12) {
         // ---------------- power group: |D2|^2 x 2^(2f), discard, stores ----------------
-        const int q = warp & 3;
+        // Warp q reads TMEM lanes 32 q .. 32 q + 31 = (n1 = lane, segment q % 2, template q / 2 of
+        // the pair); columns 4 g + (0, 1, 2, 3) = re(2g), re(2g + 1), im(2g), im(2g + 1) of n2.
+        const int q = warp & 3, sq = q & 1, zq = q >> 1;
+        const uint32_t my = tmem_lane_addr(tmem, COL_D2);
         uint32_t p = 0;
         int il = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
             const int sp = it / a.ng, grp = it % a.ng;
             const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
             wait_bar(&bar[B_SCALE0 + (il & 1)], (il >> 1) & 1, abort_flag);
-            float fsc[2] = {scl[2 * (il & 1)], scl[2 * (il & 1) + 1]};
+            const float fs = scl[2 * (il & 1) + sq];
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_SFREE0 + (il & 1)]);
-            int64_t segrow[2];
-            bool segok[2];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                segok[s] = 2 * sp + s < a.nseg;
-                segrow[s] = (int64_t)(a.seg_begin + 2 * sp + s) * a.S;
-            }
+            // outputs kept in this segment: t in [0, lim) (the step S, cut at n; none past the launch)
+            const int64_t segrow = (int64_t)(a.seg_begin + 2 * sp + sq) * a.S;
+            const int64_t left = a.n - segrow;
+            const int lim = (2 * sp + sq < a.nseg && left > 0) ? (int)(left < a.S ? left : a.S) : 0;
+            const int tbase = lane - (a.K - 1);   // output index of n2 = 0
             for (int zp = zp0; zp < zp1; ++zp, ++p) {
                 wait_bar(&bar[B_MMA2 + (p & 1)], (p >> 1) & 1, abort_flag);
                 __syncwarp();
                 if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
                 tmem_fence_after_sync();
+                const int z = 2 * zp + zq;
+                float *o = a.out + (size_t)z * (size_t)a.n + segrow;
 #pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    const int n2 = 8 * (2 * q + h) + (lane >> 2);
-                    const int tbase = 2 * (lane & 3) + 32 * n2 - (a.K - 1);
-#pragma unroll 1
-                    for (int c = 0; c < 2; ++c) {
-                        uint32_t r[32];
-                        tmem_ld_16x256_x8(tmem + ((uint32_t)(32 * q + 16 * h) << 16) + COL_D2 + 128 * (p & 1) + 64 * c, r);
-                        if (h == 1 && c == 1) {
-                            tmem_fence_before_sync();
-                            mbar_arrive(&bar[B_D2_FREE + (p & 1)]);
-                        }
-                        const int z = 2 * zp + c;
-                        if (z >= a.M) continue;
-                        float *rowp = a.out + (size_t)z * (size_t)a.n;
-                        const bool al8 = (reinterpret_cast<uintptr_t>(rowp) & 7) == 0;
+                for (int cc = 0; cc < 4; ++cc) {   // n2 = 16 cc .. 16 cc + 15
+                    uint32_t r[32];
+                    tmem_ld32(my + 128 * (p & 1) + 32 * cc, r);
+                    if (cc == 3) {
+                        tmem_fence_before_sync();
+                        mbar_arrive(&bar[B_D2_FREE + (p & 1)]);
+                    }
+                    if (z >= a.M) continue;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int s = j >> 2;
-                            const int tout = tbase + 8 * (j & 3);
-                            const int64_t idx = segrow[s] + tout;
-                            if (!segok[s] || tout < 0 || tout >= a.S || idx >= a.n) continue;
-                            const float2 re = make_float2(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]));
-                            const float2 im = make_float2(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-                            const float2 pw = pmul(pfma(re, re, pmul(im, im)), make_float2(fsc[s], fsc[s]));
-                            if (idx + 1 < a.n) {
-                                if (al8) *reinterpret_cast<float2 *>(rowp + idx) = pw;
-                                else {
-                                    rowp[idx] = pw.x;
-                                    rowp[idx + 1] = pw.y;
-                                }
-                            } else {
-                                rowp[idx] = pw.x;
-                            }
-                        }
+                    for (int g = 0; g < 8; ++g) {
+                        const float2 re = make_float2(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]));
+                        const float2 im = make_float2(__uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3]));
+                        const float2 pw = pmul(pfma(re, re, pmul(im, im)), make_float2(fs, fs));
+                        const int t0 = tbase + 32 * (16 * cc + 2 * g);
+                        if ((unsigned)t0 < (unsigned)lim) o[t0] = pw.x;
+                        if ((unsigned)(t0 + 32) < (unsigned)lim) o[t0 + 32] = pw.y;
                     }
                 }
             }
         }
-    } else if (lane == 0) {
-        // ---------------- control thread: TMA loads and MMAs ----------------
-        const uint32_t b1a = smem_u32(sm + Smem::b1), b2a = smem_u32(b2);
-        mbar_arrive_expect_tx(&bar[B_B1_FULL], B1_BYTES);
-        bulk_load(sm + Smem::b1, a.cst + CB_B1, B1_BYTES, &bar[B_B1_FULL]);
-        uint32_t seg_issued = 0;
-        auto issue_segments = [&](int it) {
-            const int sp = it / a.ng;
-            mbar_arrive_expect_tx(&bar[B_SEG_FULL], 2u * L * (uint32_t)sizeof(float2));
-#pragma unroll 1
-            for (int s = 0; s < 2; ++s) {
-                const int c0 = (a.seg_begin + 2 * sp + s) * a.S - (a.K - 1);
-#pragma unroll
-                for (int j = 0; j < L / 256; ++j) tma_load_1d(segb + s * L + 256 * j, &tmap, c0 + 256 * j, &bar[B_SEG_FULL]);
-            }
-            ++seg_issued;
-        };
-        if ((int)blockIdx.x < n_items) issue_segments(blockIdx.x);
-        bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
-        // template-load cursor, NH tiles ahead of the MMAs
-        int h_it = blockIdx.x, h_zp = 0, h_zz = 0;
-        if (h_it < n_items) h_zp = a.ZP * (h_it % a.ng) / a.ng;
-        uint32_t tH = 0, t = 0, p1 = 0, p2 = 0;
-        auto issue_mma2 = [&]() {
-            const uint32_t q = p2;
-            ok = ok && wait_bar(&bar[B_B2_FULL + (q & 1)], (q >> 1) & 1, abort_flag);
-            if (q >= 2) ok = ok && wait_bar(&bar[B_D2_FREE + (q & 1)], ((q - 2) >> 1) & 1, abort_flag);
-            if (!ok) return;
-            tmem_fence_after_sync();
-#pragma unroll
-            for (int ks = 0; ks < 8; ++ks)
-                mma_ts(tmem + COL_D2 + 128 * (q & 1), tmem + COL_A2 + 8 * ks,
-                       smem_desc(b2a + (q & 1) * B2_BYTES + ks * 2 * LBO2, LBO2, SBO2), IDESC2, ks > 0);
-            mma_commit(&bar[B_MMA2 + (q & 1)]);
-            ++p2;
-        };
-        int il = 0;
-        for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x, ++il) {
-            const int grp = it % a.ng;
-            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
-            for (int zp = zp0; ok && zp < zp1; ++zp) {
-                for (int zz = 0; ok && zz < 2; ++zz) {
-                    while (tH < t + NH && h_it < n_items) {   // template loads ahead
-                        const uint32_t slot = tH % NH;
-                        if (tH >= NH) ok = ok && wait_bar(&bar[B_H_FREE + slot], ((tH / NH) - 1) & 1, abort_flag);
-                        if (!ok) break;
-                        mbar_arrive_expect_tx(&bar[B_H_FULL + slot], H_BYTES);
-                        bulk_load(hb + slot * H_BYTES, a.H16 + (size_t)(2 * h_zp + h_zz) * H_BYTES, H_BYTES,
-                                  &bar[B_H_FULL + slot]);
-                        ++tH;
-                        if (++h_zz == 2) {
-                            h_zz = 0;
-                            if (++h_zp >= a.ZP * (h_it % a.ng + 1) / a.ng) {
-                                h_it += gridDim.x;
-                                if (h_it < n_items) h_zp = a.ZP * (h_it % a.ng) / a.ng;
-                            }
-                        }
-                    }
+    } else if (warp == 12) {
+        // ---------------- stage-1 MMA thread ----------------
+        if (lane == 0) {
+            const uint32_t b1a = smem_u32(sm + Smem::b1);
+            bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
+            uint32_t t = 0;
+            for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+                const int grp = it % a.ng;
+                const int ntiles = 2 * (a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng);
+                for (int j = 0; j < ntiles; ++j, ++t) {
                     ok = ok && wait_bar(&bar[B_A1_FULL + (t & 1)], (t >> 1) & 1, abort_flag);
-                    if (t >= 2) ok = ok && wait_bar(&bar[B_D1_FREE + (t & 1)], ((t - 2) >> 1) & 1, abort_flag);
+                    if (t >= ND1) ok = ok && wait_bar(&bar[B_D1_FREE + t % ND1], ((t - ND1) / ND1) & 1, abort_flag);
                     if (!ok) break;
                     tmem_fence_after_sync();
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
-                        mma_ts(tmem + COL_D1 + 64 * (t & 1), tmem + COL_A1 + 32 * (t & 1) + 8 * ks,
+                        mma_ts(tmem + COL_D1 + 64 * (t % ND1), tmem + COL_A1 + 32 * (t & 1) + 8 * ks,
                                smem_desc(b1a + ks * 2 * LBO1, LBO1, SBO1), IDESC1, ks > 0);
-                    mma_commit(&bar[B_MMA1 + (t & 1)]);
-                    ++t;
-                    // the product group has taken this item's spectra: load the next item's segments
-                    if (zp == zp0 && zz == 0 && it + (int)gridDim.x < n_items) {
-                        ok = ok && wait_bar(&bar[B_SEG_FREE], il & 1, abort_flag);
-                        if (ok) issue_segments(it + gridDim.x);
-                    }
+                    mma_commit(&bar[B_MMA1 + t % ND1]);
                 }
-                if (!ok) break;
-                ++p1;
-                if (p1 - p2 >= 2) issue_mma2();
+            }
+            // no MMA may be in flight when the tensor memory is released
+            for (uint32_t i = (t > ND1 ? t - ND1 : 0); i < t; ++i)
+                mbar_wait_bounded(&bar[B_MMA1 + i % ND1], (i / ND1) & 1, kWaitLimitNs);
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                atomicOr(a.status, STATUS_WAIT_TIMEOUT);
             }
         }
-        while (ok && p2 < p1) issue_mma2();
-        // nothing may be in flight when the block leaves: copies and MMAs issued land first
+    } else if (warp == 14) {
+        // ---------------- stage-2 MMA thread ----------------
+        if (lane == 0) {
+            const uint32_t b2a = smem_u32(b2), ga = smem_u32(sm + Smem::g);
+            bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
+            uint32_t q = 0;
+            for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+                const int grp = it % a.ng;
+                const int npairs = a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng;
+                for (int j = 0; j < npairs; ++j, ++q) {
+                    ok = ok && wait_bar(&bar[B_B2_FULL + (q & 1)], (q >> 1) & 1, abort_flag);
+                    if (q >= 2) ok = ok && wait_bar(&bar[B_D2_FREE + (q & 1)], ((q - 2) >> 1) & 1, abort_flag);
+                    if (!ok) break;
+                    tmem_fence_after_sync();
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks)
+                        mma_ss(tmem + COL_D2 + 128 * (q & 1), smem_desc(b2a + (q & 1) * B2_BYTES + ks * 2 * LBO2, LBO2, SBO2),
+                               smem_desc(ga + ks * 2 * LBOG, LBOG, SBOG), IDESC2, ks > 0);
+                    mma_commit(&bar[B_MMA2 + (q & 1)]);
+                }
+            }
+            for (uint32_t i = (q > 2 ? q - 2 : 0); i < q; ++i)
+                mbar_wait_bounded(&bar[B_MMA2 + (i & 1)], (i >> 1) & 1, kWaitLimitNs);
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                atomicOr(a.status, STATUS_WAIT_TIMEOUT);
+            }
+        }
+    } else if (warp == 13 && lane == 0) {
+        // ---------------- loader thread (warp 13): segments and templates by TMA ----------------
+        mbar_arrive_expect_tx(&bar[B_B1_FULL], B1_BYTES + G_BYTES);   // both DFT matrices
+        bulk_load(sm + Smem::b1, a.cst + CB_B1, B1_BYTES, &bar[B_B1_FULL]);
+        bulk_load(sm + Smem::g, a.cst + CB_G, G_BYTES, &bar[B_B1_FULL]);
+        uint32_t seg_issued = 0, tH = 0;
+        bool ok = true;
+        auto issue_segments = [&](int it) {
+            const int sp = it / a.ng;
+            mbar_arrive_expect_tx(&bar[B_SEG_FULL], 2u * L * (uint32_t)sizeof(float2));
+#pragma unroll 1
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int c0 = (a.seg_begin + 2 * sp + s2) * a.S - (a.K - 1);
+#pragma unroll
+                for (int j = 0; j < L / 256; ++j) tma_load_1d(segb + s2 * L + 256 * j, &tmap, c0 + 256 * j, &bar[B_SEG_FULL]);
+            }
+            ++seg_issued;
+        };
+        if ((int)blockIdx.x < n_items) issue_segments(blockIdx.x);
+        int il = 0;
+        for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x, ++il) {
+            const int grp = it % a.ng;
+            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+            const int ntiles = 2 * (zp1 - zp0);
+            for (int j = 0; ok && j < ntiles; ++j, ++tH) {
+                const uint32_t slot = tH % NH;
+                if (tH >= NH) ok = wait_bar(&bar[B_H_FREE + slot], ((tH / NH) - 1) & 1, abort_flag);
+                if (!ok) break;
+                mbar_arrive_expect_tx(&bar[B_H_FULL + slot], H_BYTES);
+                bulk_load(hb + slot * H_BYTES, a.H16 + (size_t)(2 * zp0 + j) * H_BYTES, H_BYTES, &bar[B_H_FULL + slot]);
+                // once the product group has taken this item's spectra, fetch the next item's segments
+                if (j == min(NH, ntiles) - 1 && it + (int)gridDim.x < n_items) {
+                    ok = wait_bar(&bar[B_SEG_FREE], il & 1, abort_flag);
+                    if (ok) issue_segments(it + gridDim.x);
+                }
+            }
+        }
+        // nothing may be in flight when the block leaves: the copies issued land first
         if (seg_issued) mbar_wait_bounded(&bar[B_SEG_FULL], (seg_issued - 1) & 1, kWaitLimitNs);
         for (uint32_t i = (tH > NH ? tH - NH : 0); i < tH; ++i)
             mbar_wait_bounded(&bar[B_H_FULL + i % NH], (i / NH) & 1, kWaitLimitNs);
-        for (uint32_t i = (t > 2 ? t - 2 : 0); i < t; ++i) mbar_wait_bounded(&bar[B_MMA1 + (i & 1)], (i >> 1) & 1, kWaitLimitNs);
-        for (uint32_t i = (p2 > 2 ? p2 - 2 : 0); i < p2; ++i)
-            mbar_wait_bounded(&bar[B_MMA2 + (i & 1)], (i >> 1) & 1, kWaitLimitNs);
         if (!ok || *abort_flag) {
             *abort_flag = 1;
             atomicOr(a.status, STATUS_WAIT_TIMEOUT);
