@@ -681,34 +681,50 @@ def bench_length_sweep(fd, dev, xd, lengths=(64, 128, 256, 421)):
 
 def bench_batch(fd, h, dev, reps=10):
     """Batched form: 64 dedispersion trials, N log-uniform in [2^18, 2^22], one persistent
-    launch per graph replay, L = 2048 and G chosen per call; beside it the autotuned plan
-    and the same 64 arrays through the per-array FP32 path (fdas_convolve)."""
+    launch per graph replay.  Rows: the FP32 plan (L = 2048, G chosen per call), the
+    autotuned FP32 plan (tuned on a proxy of this length range), the autotuner free to pick
+    the two-stage tensor-core form, the two-stage tensor-core plan, and the same arrays through
+    the per-array paths (fdas_convolve)."""
     import torch
     specs = synth.batch_trials()
     xs = [torch.from_numpy(synth.make_input(s)).to(dev) for s in specs]
     outs = [torch.empty((h.shape[0], x.numel()), dtype=torch.float32, device=dev) for x in xs]
     total_n = sum(x.numel() for x in xs)
     stream = torch.cuda.current_stream(dev)
+    alg = sum(algorithmic_bytes(x.numel(), h.shape[0]) for x in xs)
+    peak = measured_peaks()[0]
     res = {"workload": "64 arrays, N log-uniform in [2^18, 2^22] (seeds 1000+i), 85 templates",
-           "arrays": len(xs), "total_points": total_n,
-           "plane_bytes": 4 * h.shape[0] * total_n}
-    with fd.Plan(h, n_max=1 << 22) as plan:
+           "arrays": len(xs), "total_points": total_n, "plane_bytes": 4 * h.shape[0] * total_n,
+           "algorithmic_bytes": alg}
+
+    def row(plan):
         for _ in range(3):
             plan.convolve_batch(xs, outs, stream)
         ms = _events_ms(lambda: plan.convolve_batch(xs, outs, stream), reps, stream)
         plan.status(stream)
-        res.update({"seg_len": plan.desc.seg_len, "tpl_per_cta": "per call",
-                    "ms_per_batch": ms, "arrays_per_s": len(xs) / (ms / 1e3),
-                    "plane_gbs": res["plane_bytes"] / (ms / 1e3) / 1e9, "gpu_launches_per_batch": 1})
-    with fd.Plan(h, n_max=1 << 22, autotune=1) as plan:
         d = plan.desc
-        for _ in range(3):
-            plan.convolve_batch(xs, outs, stream)
-        ms = _events_ms(lambda: plan.convolve_batch(xs, outs, stream), reps, stream)
-        plan.status(stream)
-        res["autotuned"] = {"seg_len": d.seg_len, "tpl_per_cta": d.tpl_per_cta,
-                            "tune_ms": [round(v, 4) for v in d.tune_ms], "ms_per_batch": ms,
-                            "arrays_per_s": len(xs) / (ms / 1e3)}
+        return {"seg_len": d.seg_len, "tpl_per_cta": d.tpl_per_cta or "per call", "precision": d.precision,
+                "ms_per_batch": ms, "arrays_per_s": len(xs) / (ms / 1e3),
+                "plane_gbs": res["plane_bytes"] / (ms / 1e3) / 1e9, "hbm_frac": alg / (ms / 1e3) / 1e9 / peak,
+                "gpu_launches_per_batch": 1}
+
+    with fd.Plan(h, n_max=1 << 22) as plan:
+        res.update(row(plan))
+    with fd.Plan(h, n_max=1 << 22, autotune=1, tune_n_min=1 << 18) as plan:
+        res["autotuned"] = row(plan)
+        res["autotuned"]["tune_ms"] = [round(v, 4) for v in plan.desc.tune_ms]
+    with fd.Plan(h, n_max=1 << 22, autotune=2, tune_n_min=1 << 18) as plan:
+        res["autotuned_with_precision"] = row(plan)
+        res["autotuned_with_precision"]["tune_ms_tc"] = round(plan.desc.tune_ms_tc, 4)
+    with fd.Plan(h, n_max=1 << 22, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        res["tensor_core"] = row(plan)
+
+        def per_array_tc():
+            for x, o in zip(xs, outs):
+                plan.convolve(x, o, stream)
+        per_array_tc()
+        ms1 = _events_ms(per_array_tc, max(2, reps // 2), stream)
+        res["tensor_core"].update({"per_array_ms": ms1, "per_array_arrays_per_s": len(xs) / (ms1 / 1e3)})
     with fd.Plan(h, n_max=1 << 22) as plan:
         def per_array():
             for x, o in zip(xs, outs):
@@ -722,9 +738,16 @@ def bench_batch(fd, h, dev, reps=10):
 
 
 def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=32, stress_budget=4e9,
-                stress_requests=300):
+                stress_requests=300, precision=None):
     """Served form: Poisson arrivals at `rate`, N log-uniform in [2^16, 2^22], admission by
-    plane memory within `budget`; requests cycle over `pool_size` distinct arrays."""
+    plane memory within `budget`; requests cycle over `pool_size` distinct arrays.  With
+    `precision` None, the FP32 plan and then the two-stage tensor-core plan."""
+    if precision is None:
+        res = bench_serve(fd, h, dev, rate, duration, budget, pool_size, stress_budget, stress_requests,
+                          fd.FDAS_PREC_FP32)
+        res["tensor_core"] = bench_serve(fd, h, dev, rate, duration, budget, pool_size, stress_budget,
+                                         stress_requests, fd.FDAS_PREC_TC_DFT2)
+        return res
     import queue
     import threading
     import torch
@@ -734,7 +757,7 @@ def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=3
     res = {"workload": f"Poisson {rate:g} arrays/s for {duration:g} s ({count} requests), N log-uniform in "
                        f"[2^16, 2^22] (arrival seed 2000, {pool_size} distinct arrays 2001+i), budget "
                        f"{budget / 1e9:g} GB", "requests": count}
-    with fd.Plan(h, n_max=1 << 22) as plan:
+    with fd.Plan(h, n_max=1 << 22, precision=precision) as plan:
         stream = torch.cuda.current_stream(dev)
         outs = [torch.empty((h.shape[0], x.numel()), dtype=torch.float32, device=dev) for x in pool]
 
@@ -744,8 +767,8 @@ def bench_serve(fd, h, dev, rate=200.0, duration=10.0, budget=120e9, pool_size=3
         per_array()
         ms1 = _events_ms(per_array, 3, stream)
         mean_n = np.mean([x.numel() for x in pool])
-        res["per_array_fp32_ms_mean"] = ms1 / len(pool)
-        res["per_array_fp32_capacity_arrays_per_s"] = len(pool) / (ms1 / 1e3)
+        res["per_array_ms_mean"] = ms1 / len(pool)
+        res["per_array_capacity_arrays_per_s"] = len(pool) / (ms1 / 1e3)
         del outs
 
         def run(srv, times):

@@ -58,16 +58,20 @@ typedef struct {
                          of segments (all M for long arrays, fewer per block for short ones so
                          that the launch still fills the GPU; the tensor-core form uses all M) */
     int precision;    /* FDAS_PREC_* (0 = FP32) */
-    int autotune;     /* 1: time every (L in {1024, 2048, 4096}) x (G in {5, 17, 85}) with the
-                         persistent kernel on one array of min(n_max, 2^21) points and keep the
-                         fastest (seg_len is then ignored; a non-zero tpl_per_cta stays fixed);
-                         results are cached per process by (device, M, K, tuning length) */
+    int autotune;     /* 1: time every (L in {1024, 2048, 4096}) x (G chosen per call, 5, 17, 85)
+                         with the persistent batch kernel on a seeded proxy of the batches the
+                         plan will serve (16 arrays, lengths log-uniform in [tune_n_min, n_max])
+                         and keep the fastest (seg_len is then ignored; a non-zero tpl_per_cta
+                         stays fixed); 2: the same, with the two-stage tensor-core form
+                         (FDAS_PREC_TC_DFT2, L = 2048, its 2e-3 tolerance) as one more candidate.
+                         Results are cached per process by (device, M, K, lengths, mode, G) */
     int group_support;/* 1: group the templates by the length of their nonzero support, each
                          group with its own overlap-save frame and step and its templates stored
                          shifted to their first nonzero tap (fewer inverse FFTs when supports
                          differ); one launch per group.  FP32 form, without autotuning; used by
                          fdas_convolve, fdas_convolve_host and fdas_convolve_candidates (the
                          batched and served forms return FDAS_ERR_UNSUPPORTED for such a plan) */
+    int64_t tune_n_min;  /* autotuner: shortest array of the proxy batch (0 = n_max / 16) */
 } fdas_opts;
 
 /* Read-only description of a plan. */
@@ -83,8 +87,9 @@ typedef struct {
     int     precision;    /* FDAS_PREC_* */
     int     device;       /* CUDA device ordinal the plan lives on */
     int64_t device_bytes; /* device memory owned by the plan */
-    int     tuned;        /* 1 if the autotuner chose seg_len and tpl_per_cta */
-    float   tune_ms[9];   /* autotuner: ms per plane of its tuning array, [L in 1024, 2048, 4096][G in 5, 17, 85] (0 = not run) */
+    int     tuned;        /* 1 if the autotuner chose seg_len, tpl_per_cta (and precision) */
+    float   tune_ms[12];  /* autotuner: ms per proxy batch, [L in 1024, 2048, 4096][G in per call, 5, 17, 85] (0 = not run) */
+    float   tune_ms_tc;   /* autotuner (mode 2): ms per proxy batch of the two-stage tensor-core form */
     int     batch_blocks; /* blocks of the persistent batch kernel (resident blocks per SM x SMs) */
     int     groups;       /* template groups = kernel launches per plane (1 unless group_support) */
 } fdas_plan_desc;
@@ -196,15 +201,17 @@ int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *o
  *   The three arrays of pointers/lengths are host memory, read during the call.
  *
  * Enqueues, per group of up to 120 arrays, one replay of the plan's CUDA graph
- * [reset the work counter -> persistent kernel with one block per resident slot]; the
- * kernel's blocks take work items (array, template group, segment) from the counter.
- * Each template's arithmetic is that of fdas_convolve (whatever the templates per block),
- * so results equal those of fdas_convolve on each array bit for bit.  Asynchronous.  Calls on one plan are serialised by the library on the
+ * [reset the work counter -> persistent kernel with one block per resident slot].  FP32
+ * plans: the kernel's blocks take work items (array, template group, segment) from the
+ * counter.  FDAS_PREC_TC_DFT2 plans: one block per SM takes items (array, segment pair,
+ * template-pair group) in turn by block index.  Each template's arithmetic is that of
+ * fdas_convolve (whatever the grouping), so results equal those of fdas_convolve on each
+ * array bit for bit.  Asynchronous.  Calls on one plan are serialised by the library on the
  * host; their kernels run in stream order and must not overlap in time: do not
  * issue batches of one plan on two streams that run concurrently.
  * Errors: INVALID_ARG (any entry invalid: nothing is enqueued), UNSUPPORTED (a plan
- * created with group_support, or a plan whose precision this form is not built for;
- * nothing is enqueued), CUDA.
+ * created with group_support, or an FDAS_PREC_TC_FP16 plan, for which this form is not
+ * built; nothing is enqueued), CUDA.
  */
 int fdas_convolve_batch(fdas_plan p, int count, const void *const *ins, const int64_t *ns,
                         float *const *outs, void *stream);
@@ -354,8 +361,8 @@ typedef struct {
 } fdas_server_report;
 
 /* Create a server (starts its scheduler thread; reserves budget_bytes on the plan's
- * device).  Errors: INVALID_ARG, UNSUPPORTED (a grouped plan, or a plan whose precision the
- * batched form is not built for), OOM, CUDA. */
+ * device).  FP32 and FDAS_PREC_TC_DFT2 plans.  Errors: INVALID_ARG, UNSUPPORTED (a grouped
+ * plan, or an FDAS_PREC_TC_FP16 plan), OOM, CUDA. */
 int fdas_server_create(fdas_server *out, fdas_plan plan, const fdas_server_opts *opts);
 
 /* Queue one request.  in_c64_dev: device complex64 [n], 16-byte aligned, valid until

@@ -124,8 +124,10 @@ struct fdas_plan_s {
     fdas::BatchKernel bk;
     int bk_version = 0;                     // bumped whenever bk changes (graphs must be rebuilt)
     fdas::Lane lane0;
-    // autotuner results, ms per plane of the tuning array, [L index][G index]
-    float tune_ms[3][3] = {};
+    // autotuner results, ms per proxy batch, [L index][G index: per call, 5, 17, 85], and the
+    // two-stage tensor-core form
+    float tune_ms[3][4] = {};
+    float tune_ms_tc = 0.f;
     int tuned = 0;
     // host-buffer entry point
     std::mutex host_mu;
@@ -345,6 +347,8 @@ int build_templates(fdas_plan p, const float2 *d_h32, int L)
     p->bk = fdas::BatchKernel();
     p->bk_version++;
     if ((e = fdas::batch_kernel(L, &p->bk)) != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
+    if (p->precision == FDAS_PREC_TC_DFT2 && (e = fdas::tc2_batch_kernel(&p->bk)) != cudaSuccess)
+        return cuda_fail(e, "tensor-core batch kernel attributes");
     return FDAS_OK;
 }
 
@@ -352,8 +356,8 @@ int validate_batch(fdas_plan p, int count, const void *const *ins, const int64_t
 {
     if (!p) return fail(FDAS_ERR_INVALID_ARG, "null plan");
     if (p->d_rows) return fail(FDAS_ERR_UNSUPPORTED, "the batched forms are built for ungrouped plans");
-    if (p->precision != FDAS_PREC_FP32)
-        return fail(FDAS_ERR_UNSUPPORTED, "the batched forms are built for FP32 plans (precision %d)", p->precision);
+    if (p->precision == FDAS_PREC_TC_FP16)
+        return fail(FDAS_ERR_UNSUPPORTED, "the batched forms are not built for the single-pass tensor-core form");
     if (count < 0 || (count > 0 && (!ins || !ns || !outs))) return fail(FDAS_ERR_INVALID_ARG, "bad batch arrays");
     for (int i = 0; i < count; ++i) {
         int rc = validate_convolve(p, ins[i], ns[i], outs[i]);
@@ -368,83 +372,147 @@ int enqueue_batch(fdas_plan p, int count, const void *const *ins, const int64_t 
     return fdas::lane_launch(p, &p->lane0, count, ins, ns, outs, stream);
 }
 
-// Autotuner: time the persistent kernel for every (L, G) candidate on one array of
-// min(n_max, 2^21) points and keep the fastest; results are cached per process by
-// (device, M, K, tuning length).
+// Autotuner: time the persistent batch kernel for every (L, G) candidate -- G = 0 being the
+// per-call choice -- and, with mode 2, the two-stage tensor-core form (L = 2048), on a seeded
+// proxy of the batches the plan will serve: 16 arrays with lengths log-uniform in [n_min,
+// n_max]; keep the fastest.  Results are cached per process by (device, M, K, n_min, n_max,
+// mode, fixed G).
 struct TuneKey {
-    int dev, M, K;
-    int64_t n;
+    int dev, M, K, mode, fixed_G;
+    int64_t n_min, n_max;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(dev, M, K, n) < std::tie(o.dev, o.M, o.K, o.n);
+        return std::tie(dev, M, K, mode, fixed_G, n_min, n_max) < std::tie(o.dev, o.M, o.K, o.mode, o.fixed_G, o.n_min, o.n_max);
     }
 };
 struct TuneVal {
-    int L, G;
-    float ms[3][3];
+    int L, G, precision;
+    float ms[3][4], ms_tc;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
 
 const int kTuneL[3] = {1024, 2048, 4096};
-const int kTuneG[3] = {5, 17, 85};
+const int kTuneG[4] = {0, 5, 17, 85};
+constexpr int kTuneArrays = 16;
 
-int autotune(fdas_plan p, const float2 *d_h32, int fixed_G)
+// Lengths of the proxy batch: log-uniform in [lo, hi] from a fixed splitmix64 sequence.
+std::vector<int64_t> tune_lengths(int64_t lo, int64_t hi)
 {
-    const int64_t n = std::min<int64_t>(p->n_max, int64_t(1) << 21);
-    const TuneKey key{p->device, p->M, p->K_user, n};
+    std::vector<int64_t> ns(kTuneArrays);
+    uint64_t x = 0x243F6A8885A308D3ull;
+    for (auto &n : ns) {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double u = (double)(z >> 11) / 9007199254740992.0;
+        n = (int64_t)std::llround(std::exp(std::log((double)lo) + u * (std::log((double)hi) - std::log((double)lo))));
+        n = std::max(lo, std::min(hi, n));
+    }
+    return ns;
+}
+
+int tc2_resources(fdas_plan p)   // the two-stage form's constants and fp16 spectra (allocated once)
+{
+    cudaError_t e;
+    if (!p->d_tc2c && (e = cudaMalloc(&p->d_tc2c, fdas::tc2_const_bytes())) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc tensor-core constants");
+    if (!p->d_H16 && (e = cudaMalloc(&p->d_H16, fdas::tc2_template_bytes(p->M))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc fp16 template spectra");
+    if ((e = fdas::launch_tc2_constants(p->d_tc2c, nullptr)) != cudaSuccess) return cuda_fail(e, "tensor-core constants kernel");
+    return FDAS_OK;
+}
+
+int autotune(fdas_plan p, const float2 *d_h32, int fixed_G, int mode, int64_t n_min)
+{
+    const int64_t n_max = p->n_max;
+    n_min = n_min > 0 ? std::min(n_min, n_max) : std::max<int64_t>(1, n_max / 16);
+    const TuneKey key{p->device, p->M, p->K_user, mode, fixed_G, n_min, n_max};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end() && !fixed_G) {
+        if (it != g_tune_cache.end()) {
             p->L = it->second.L;
-            p->G = it->second.G;
+            p->G = it->second.G ? it->second.G : p->M;
+            p->g_auto = it->second.G == 0;
+            p->precision = it->second.precision;
             std::memcpy(p->tune_ms, it->second.ms, sizeof p->tune_ms);
+            p->tune_ms_tc = it->second.ms_tc;
             p->tuned = 1;
-            return FDAS_OK;
+            return p->precision == FDAS_PREC_TC_DFT2 ? tc2_resources(p) : FDAS_OK;
         }
     }
+    const std::vector<int64_t> ns = tune_lengths(n_min, n_max);
     void *d_in = nullptr;
     float *d_out = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_in, sizeof(float2) * n)) != cudaSuccess) return cuda_fail(e, "autotune input");
-    if ((e = cudaMalloc(&d_out, sizeof(float) * n * p->M)) != cudaSuccess) {
+    if ((e = cudaMalloc(&d_in, sizeof(float2) * n_max)) != cudaSuccess) return cuda_fail(e, "autotune input");
+    if ((e = cudaMalloc(&d_out, sizeof(float) * n_max * p->M)) != cudaSuccess) {
         cudaFree(d_in);
         return cuda_fail(e, "autotune output");
     }
-    cudaMemset(d_in, 0x3c, sizeof(float2) * n);   // finite, non-denormal values
+    cudaMemset(d_in, 0x3c, sizeof(float2) * n_max);   // finite, non-denormal values
+    // every proxy array reads a prefix of one input and writes one shared plane buffer: only
+    // the time is kept
+    std::vector<const void *> ins(kTuneArrays, d_in);
+    std::vector<float *> outs(kTuneArrays, d_out);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bestL = p->L, bestG = p->G, rc = FDAS_OK;
-    const void *ins[1] = {d_in};
-    const int64_t ns[1] = {n};
-    float *outs[1] = {d_out};
+    int bestL = p->L, bestG = p->G, bestP = FDAS_PREC_FP32, rc = FDAS_OK;
+    auto time_batch = [&](float *out_ms) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 4 && rc == FDAS_OK; ++rep) {
+            cudaEventRecord(e0, nullptr);
+            rc = enqueue_batch(p, kTuneArrays, ins.data(), ns.data(), outs.data(), nullptr);
+            cudaEventRecord(e1, nullptr);
+            if (rc == FDAS_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune run");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t / 3.f;
+        }
+        *out_ms = ms;
+    };
     for (int li = 0; li < 3 && rc == FDAS_OK; ++li) {
         const int L = kTuneL[li];
         if (p->K > L - 4) continue;
+        p->precision = FDAS_PREC_FP32;
         if ((rc = build_templates(p, d_h32, L))) break;
-        for (int gi = 0; gi < 3 && rc == FDAS_OK; ++gi) {
+        for (int gi = 0; gi < 4 && rc == FDAS_OK; ++gi) {
             const int G = fixed_G ? fixed_G : std::min(kTuneG[gi], p->M);
-            p->G = G;
+            p->g_auto = G == 0;
+            p->G = G ? G : p->M;
             float ms = 0.f;
-            for (int rep = 0; rep < 4 && rc == FDAS_OK; ++rep) {
-                cudaEventRecord(e0, nullptr);
-                rc = enqueue_batch(p, 1, ins, ns, outs, nullptr);
-                cudaEventRecord(e1, nullptr);
-                if (rc == FDAS_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune run");
-                float t = 0.f;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (rep > 0) ms += t / 3.f;
-            }
+            time_batch(&ms);
             p->tune_ms[li][gi] = ms;
             if (rc == FDAS_OK && ms < best) {
                 best = ms;
                 bestL = L;
                 bestG = G;
+                bestP = FDAS_PREC_FP32;
             }
             if (fixed_G) break;
+        }
+    }
+    if (rc == FDAS_OK && mode == 2 && p->K <= 2048 - 4) {   // the two-stage tensor-core form
+        p->precision = FDAS_PREC_TC_DFT2;
+        p->g_auto = 0;
+        p->G = p->M;
+        if (!(rc = tc2_resources(p)) && !(rc = build_templates(p, d_h32, 2048))) {
+            if ((e = fdas::launch_tc2_pretransform(d_h32, p->M, p->K_user, p->d_tw64, p->eH, p->d_H16, nullptr)) != cudaSuccess)
+                rc = cuda_fail(e, "fp16 template pre-transform");
+            float ms = 0.f;
+            if (rc == FDAS_OK) time_batch(&ms);
+            p->tune_ms_tc = ms;
+            if (rc == FDAS_OK && ms < best) {
+                best = ms;
+                bestL = 2048;
+                bestG = 0;
+                bestP = FDAS_PREC_TC_DFT2;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -454,20 +522,74 @@ int autotune(fdas_plan p, const float2 *d_h32, int fixed_G)
     if (rc != FDAS_OK) return rc;
     if ((rc = fdas_plan_status(p, nullptr)) != FDAS_OK) return rc;
     p->L = bestL;
-    p->G = bestG;
+    p->precision = bestP;
+    p->g_auto = bestP == FDAS_PREC_FP32 && bestG == 0;
+    p->G = bestG ? bestG : p->M;
+    if (bestP != FDAS_PREC_TC_DFT2) {   // the tensor-core candidate's buffers are not kept
+        cudaFree(p->d_tc2c);
+        cudaFree(p->d_H16);
+        p->d_tc2c = nullptr;
+        p->d_H16 = nullptr;
+    }
     p->tuned = 1;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (!fixed_G) {
-        TuneVal v{bestL, bestG, {}};
-        std::memcpy(v.ms, p->tune_ms, sizeof v.ms);
-        g_tune_cache[key] = v;
-    }
+    TuneVal v{bestL, bestG, bestP, {}, p->tune_ms_tc};
+    std::memcpy(v.ms, p->tune_ms, sizeof v.ms);
+    g_tune_cache[key] = v;
     return FDAS_OK;
 }
 
 }  // namespace
 
 namespace fdas {
+
+// Fill the table and launch arguments of one persistent launch over arrays [first, first + cnt).
+// FP32 plans: items (array, template group, segment), G from the total segment count.  Two-stage
+// tensor-core plans: items (array, segment pair, template-pair group), the groups per segment
+// pair from the total number of segment pairs.
+static int fill_batch(fdas_plan p, BatchTable &t, OlsArgs &a, int first, int cnt, const void *const *ins,
+                      const int64_t *ns, float *const *outs)
+{
+    a = OlsArgs();
+    a.H = p->d_H;
+    a.tw = p->d_tw;
+    a.M = p->M;
+    a.S = p->S;
+    a.K = p->K;
+    a.status = p->d_status;
+    const bool tc2 = p->precision == FDAS_PREC_TC_DFT2;
+    int64_t units = 0;   // segments (FP32) or segment pairs (tensor-core form)
+    for (int i = 0; i < cnt; ++i) {
+        const int64_t ns_i = n_segments(p, ns[first + i]);
+        units += tc2 ? (ns_i + 1) / 2 : ns_i;
+    }
+    int per_unit;
+    if (tc2) {
+        a.H16 = p->d_H16;
+        a.cst = p->d_tc2c;
+        a.eH = p->eH;
+        a.ng = tc2_groups_for(units, p->M);
+        a.G = p->M;
+        per_unit = a.ng;
+    } else {
+        a.G = call_G(p, units, p->M);
+        per_unit = (p->M + a.G - 1) / a.G;
+    }
+    int64_t items = 0;
+    for (int i = 0; i < cnt; ++i) {
+        BatchArray &ar = t.arr[i];
+        int rc = encode_input_map(&ar.map, ins[first + i], ns[first + i]);
+        if (rc) return rc;
+        ar.out = outs[first + i];
+        ar.n = ns[first + i];
+        ar.nseg = (int)n_segments(p, ar.n);
+        ar.item_off = items;
+        items += (int64_t)(tc2 ? (ar.nseg + 1) / 2 : ar.nseg) * per_unit;
+    }
+    t.count = cnt;
+    t.total_items = items;
+    return FDAS_OK;
+}
 
 // Direct (graph-free) launches of the persistent batch kernel, one per table of up to
 // kBatchMax arrays; launch c takes its work counter at counters[c].  The counters are
@@ -486,31 +608,10 @@ int batch_direct(fdas_plan p, int count, const void *const *ins, const int64_t *
     if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * chunks, stream)) != cudaSuccess)
         return cuda_fail(e, "clear work counters");
     BatchTable t;
-    OlsArgs a = {};
-    a.H = p->d_H;
-    a.tw = p->d_tw;
-    a.M = p->M;
-    a.S = p->S;
-    a.K = p->K;
-    a.status = p->d_status;
+    OlsArgs a;
     for (int c = 0; c < chunks; ++c) {
         const int first = c * kBatchMax, cnt = std::min(kBatchMax, count - first);
-        int64_t segs = 0;
-        for (int i = 0; i < cnt; ++i) segs += n_segments(p, ns[first + i]);
-        a.G = call_G(p, segs, p->M);
-        const int ngroups = (p->M + a.G - 1) / a.G;
-        int64_t items = 0;
-        for (int i = 0; i < cnt; ++i) {
-            BatchArray &ar = t.arr[i];
-            if ((rc = encode_input_map(&ar.map, ins[first + i], ns[first + i]))) return rc;
-            ar.out = outs[first + i];
-            ar.n = ns[first + i];
-            ar.nseg = (int)n_segments(p, ar.n);
-            ar.item_off = items;
-            items += (int64_t)ar.nseg * ngroups;
-        }
-        t.count = cnt;
-        t.total_items = items;
+        if ((rc = fill_batch(p, t, a, first, cnt, ins, ns, outs))) return rc;
         int *counter = counters + c;
         void *args[3] = {&t, &a, &counter};
         if ((e = cudaLaunchKernel(p->bk.fn, dim3(p->bk.resident), dim3(p->bk.block), args, p->bk.smem, stream)) !=
@@ -575,33 +676,8 @@ static int lane_ensure(fdas_plan p, Lane *l)
 static int lane_chunk(fdas_plan p, Lane *l, int first, int cnt, const void *const *ins, const int64_t *ns,
                       float *const *outs, cudaStream_t stream)
 {
-    BatchTable &t = *l->table;
-    int64_t segs = 0;
-    for (int i = 0; i < cnt; ++i) segs += n_segments(p, ns[first + i]);
-    const int G = call_G(p, segs, p->M);
-    const int ngroups = (p->M + G - 1) / G;
-    int64_t items = 0;
-    for (int i = 0; i < cnt; ++i) {
-        BatchArray &a = t.arr[i];
-        int rc = encode_input_map(&a.map, ins[first + i], ns[first + i]);
-        if (rc) return rc;
-        a.out = outs[first + i];
-        a.n = ns[first + i];
-        a.nseg = (int)n_segments(p, a.n);
-        a.item_off = items;
-        items += (int64_t)a.nseg * ngroups;
-    }
-    t.count = cnt;
-    t.total_items = items;
-    OlsArgs &a = l->args;
-    a = OlsArgs();
-    a.H = p->d_H;
-    a.tw = p->d_tw;
-    a.M = p->M;
-    a.G = G;
-    a.S = p->S;
-    a.K = p->K;
-    a.status = p->d_status;
+    int rc = fill_batch(p, *l->table, l->args, first, cnt, ins, ns, outs);
+    if (rc) return rc;
     void *args[3] = {l->table, &l->args, &l->d_counter};
     cudaKernelNodeParams kp = {};
     kp.func = const_cast<void *>(p->bk.fn);
@@ -684,6 +760,8 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
     if (n_max < 1 || n_max > (int64_t(1) << 30)) return fail(FDAS_ERR_INVALID_ARG, "n_max=%lld outside [1, 2^30]", (long long)n_max);
     if (o.tpl_per_cta < 0 || o.tpl_per_cta > M) return fail(FDAS_ERR_INVALID_ARG, "tpl_per_cta=%d outside [0, %d]", o.tpl_per_cta, M);
     if (o.group_support != 0 && o.group_support != 1) return fail(FDAS_ERR_INVALID_ARG, "group_support=%d not 0 or 1", o.group_support);
+    if (o.autotune < 0 || o.autotune > 2) return fail(FDAS_ERR_INVALID_ARG, "autotune=%d not 0, 1 or 2", o.autotune);
+    if (o.tune_n_min < 0) return fail(FDAS_ERR_INVALID_ARG, "tune_n_min=%lld < 0", (long long)o.tune_n_min);
     if (o.group_support && (o.precision != FDAS_PREC_FP32 || o.autotune))
         return fail(FDAS_ERR_UNSUPPORTED, "template groups are built for the FP32 form without autotuning");
 
@@ -723,9 +801,8 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
         if ((e = cudaMalloc(&p->d_wtc, fdas::tc_matrix_bytes())) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc DFT matrices");
         else if ((e = fdas::launch_tc_matrices(p->d_wtc, nullptr)) != cudaSuccess) rc = cuda_fail(e, "DFT matrix kernel");
     }
-    if (rc == FDAS_OK && p->precision == FDAS_PREC_TC_DFT2) {
-        // template scale 2^eH: the largest power of two with 2^eH max_z sum_k |h_z[k]| <= 16,
-        // which bounds every |FFT(h_z)[f]| 2^eH by 16 (fp16 operand range)
+    {   // two-stage tensor-core form's template scale 2^eH: the largest power of two with
+        // 2^eH max_z sum_k |h_z[k]| <= 16, which bounds every |FFT(h_z)[f]| 2^eH by 16 (fp16 range)
         const float2 *hh = static_cast<const float2 *>(templates);
         double l1max = 0.0;
         for (int z = 0; z < M; ++z) {
@@ -735,12 +812,9 @@ int fdas_plan_create(fdas_plan *out, int64_t n_max, const void *templates, int M
         }
         p->eH = l1max > 0.0 ? (int)std::floor(std::log2(16.0 / l1max)) : 0;
         p->eH = std::max(-60, std::min(60, p->eH));
-        if ((e = cudaMalloc(&p->d_tc2c, fdas::tc2_const_bytes())) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc tensor-core constants");
-        else if ((e = cudaMalloc(&p->d_H16, fdas::tc2_template_bytes(M))) != cudaSuccess)
-            rc = cuda_fail(e, "cudaMalloc fp16 template spectra");
-        else if ((e = fdas::launch_tc2_constants(p->d_tc2c, nullptr)) != cudaSuccess) rc = cuda_fail(e, "tensor-core constants kernel");
     }
-    if (rc == FDAS_OK && o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta);
+    if (rc == FDAS_OK && p->precision == FDAS_PREC_TC_DFT2) rc = tc2_resources(p);
+    if (rc == FDAS_OK && o.autotune) rc = autotune(p, d_h32, o.tpl_per_cta, o.autotune, o.tune_n_min);
     p->d_h32 = d_h32;   // kept for the time-domain form
     if (rc == FDAS_OK && o.group_support) {
         // transform the permuted, shifted templates instead of the raw ones
@@ -790,7 +864,8 @@ int fdas_plan_describe(fdas_plan p, fdas_plan_desc *d)
     d->device = p->device;
     d->device_bytes = p->device_bytes;
     d->tuned = p->tuned;
-    for (int i = 0; i < 9; ++i) d->tune_ms[i] = p->tune_ms[i / 3][i % 3];
+    for (int i = 0; i < 12; ++i) d->tune_ms[i] = p->tune_ms[i / 4][i % 4];
+    d->tune_ms_tc = p->tune_ms_tc;
     d->batch_blocks = p->bk.resident;
     d->groups = p->ngroups;
     return FDAS_OK;

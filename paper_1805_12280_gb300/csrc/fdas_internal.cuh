@@ -60,6 +60,11 @@ struct OlsArgs {
     // by shifts[z] (the first nonzero tap); outputs before the shift are zero
     const int *rows = nullptr;
     const int *shifts = nullptr;
+    // two-stage tensor-core form: fp16 template spectra, plan constants, their scale and the
+    // template-pair groups per segment pair
+    const unsigned char *H16 = nullptr;
+    const unsigned char *cst = nullptr;
+    int eH = 0, ng = 1;
 };
 
 // One array of a batch: its input tensor map (param space), output plane and work items.
@@ -140,6 +145,10 @@ cudaError_t launch_tc2_pretransform(const float2 *h32, int M, int K, const doubl
                                     cudaStream_t s);
 cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &a, const unsigned char *H16,
                            const unsigned char *cst, int eH, int nseg, cudaStream_t s);
+// Its persistent batch kernel (same parameters as the FP32 one) and the template-pair groups
+// per segment pair for a launch over n_sp segment pairs.
+cudaError_t tc2_batch_kernel(BatchKernel *k);
+int tc2_groups_for(int64_t n_sp, int M);
 
 // Time-domain form (Eq. 1 term by term) over the raw templates h [M][K].
 cudaError_t launch_td_direct(const float2 *x, int64_t n, const float2 *h, int M, int K, float *out, cudaStream_t s);

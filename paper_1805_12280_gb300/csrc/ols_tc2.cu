@@ -72,9 +72,8 @@ enum : int {
     B_SEG_FULL = 0, B_SEG_FREE, B_B1_FULL,
     B_SCALE0, B_SCALE1, B_SFREE0, B_SFREE1,   // per-item power factors: written / read
     B_H_FULL, B_H_FREE = B_H_FULL + NH,
-    B_A1_FULL = B_H_FREE + NH, B_MMA1 = B_A1_FULL + 2, B_D1_FREE = B_MMA1 + ND1,
-    B_B2_FULL = B_D1_FREE + ND1, B_MMA2 = B_B2_FULL + 2, B_D2_FREE = B_MMA2 + 2,
-    B_COUNT = B_D2_FREE + 2
+    B_MMA1 = B_H_FREE + NH, B_MMA2 = B_MMA1 + ND1,   // tcgen05.commit: stage 1 of tile t, stage 2 of pair q
+    B_COUNT = B_MMA2 + 2
 };
 
 struct Smem {
@@ -97,13 +96,46 @@ struct Args {
     const unsigned char *H16;   // [M even][64][36] half2 per template, times 2^eH
     const unsigned char *cst;   // plan constants (CONST_BYTES)
     const float2 *tw;           // [L] W_L^e = exp(-2 pi i e / L), FP32 (forward FFT)
-    float *out;                 // [M][n]
-    int64_t n;
     int M, S, K;                // templates, segment step, frame length
-    int seg_begin, nseg;        // segments [seg_begin, seg_begin + nseg) of this launch
-    int n_sp, ng, ZP;           // segment pairs, template-pair groups per pair, template pairs
+    int ng, ZP;                 // template-pair groups per segment pair, template pairs
     int eH;                     // template scale exponent
     int *status;
+};
+
+// A work item: template-pair group `grp` of segment pair `sp` of one array.
+struct Item {
+    const CUtensorMap *map;     // the array's input tensor map
+    float *out;                 // its plane [M][n]
+    int64_t n;
+    int seg_begin, nseg;        // the segments [seg_begin, seg_begin + nseg) this launch covers
+    int sp, grp;
+};
+// One array (fdas_convolve): items (sp, grp) in order, sp = it / ng.
+struct SingleSrc {
+    const CUtensorMap *map;
+    float *out;
+    int64_t n;
+    int seg_begin, nseg, n_sp, ng;
+    __device__ __forceinline__ int count() const { return n_sp * ng; }
+    __device__ __forceinline__ Item item(int it) const { return Item{map, out, n, seg_begin, nseg, it / ng, it % ng}; }
+};
+// Many arrays (fdas_convolve_batch): array i owns items [item_off_i, item_off_i + n_sp_i ng).
+struct BatchSrc {
+    const BatchTable *t;
+    int ng;
+    __device__ __forceinline__ int count() const { return (int)t->total_items; }
+    __device__ __forceinline__ Item item(int it) const
+    {
+        int lo = 0, hi = t->count - 1;   // the last array whose first item is <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (t->arr[mid].item_off <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchArray &b = t->arr[lo];
+        const int local = it - (int)b.item_off;
+        return Item{&b.map, b.out, b.n, 0, b.nseg, local / ng, local % ng};
+    }
 };
 
 __host__ __device__ inline uint32_t b1_off(int j, int k)
@@ -160,6 +192,15 @@ __device__ __forceinline__ bool p_all(bool ok)
                  : "memory");
     return r != 0;
 }
+
+// Named hardware barriers for the handoffs between warps (a producer group of 128 threads
+// arrives, the consumer warp syncs): they wake the consumer far sooner than an mbarrier.
+// Every role runs its loops to the end, skipping work once the abort flag is set but still
+// arriving, so that no consumer waits on an arrival that never comes.
+enum : int { NB_A1 = 2, NB_D1 = 4, NB_B2 = 7, NB_D2 = 9 };   // A1 x 2, D1 x 3, B2 x 2, D2 x 2
+constexpr int NB_COUNT = NT + 32;
+__device__ __forceinline__ void nb_arrive(int id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(NB_COUNT) : "memory"); }
+__device__ __forceinline__ void nb_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(NB_COUNT) : "memory"); }
 
 // Bounded wait that also returns early once another role has given up (abort flag set).
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort)
@@ -251,8 +292,8 @@ __global__ void tc2_pretransform_kernel(const float2 *__restrict__ h32, int M, i
 // The segment kernel: one block per SM, work items (segment pair, template-pair range) taken
 // round-robin by block index.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(tc2::kThreads, 1)
-    ols_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const tc2::Args a)
+template <class Src>
+__device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
 {
     using namespace tc2;
     extern __shared__ unsigned char smem_raw[];
@@ -268,7 +309,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Smem::misc + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_items = a.n_sp * a.ng;
+    const int n_items = src.count();
     constexpr int CTRL = 3 * NT;   // the MMA thread initialises the barriers
 
     if (tid == CTRL) {
@@ -283,16 +324,9 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             mbar_init(&bar[B_H_FULL + i], 1);
             mbar_init(&bar[B_H_FREE + i], NT);
         }
-        for (int i = 0; i < (int)ND1; ++i) {
+        for (int i = 0; i < (int)ND1; ++i)
             mbar_init(&bar[B_MMA1 + i], 1);        // stage 1 of tile t done: D1[t % 3] full, A1[t % 2] free
-            mbar_init(&bar[B_D1_FREE + i], NT);
-        }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar[B_A1_FULL + i], NT);
-            mbar_init(&bar[B_B2_FULL + i], NT);
-            mbar_init(&bar[B_MMA2 + i], 1);
-            mbar_init(&bar[B_D2_FREE + i], NT);
-        }
+        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_MMA2 + i], 1);   // stage 2 of pair q: D2 full, B2 free
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -308,10 +342,12 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         uint32_t t = 0;
         int il = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
-            if (!p_all(!*abort_flag)) break;
-            const int grp = it % a.ng;
+            const int grp = src.item(it).grp;
             const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
-            if (!p_all(wait_bar(&bar[B_SEG_FULL], il & 1, abort_flag))) break;
+            if (!p_all(!*abort_flag && wait_bar(&bar[B_SEG_FULL], il & 1, abort_flag))) {
+                for (int j = 0; j < 2 * (zp1 - zp0); ++j, ++t) nb_arrive(NB_A1 + (t & 1));   // keep the handoffs
+                continue;
+            }
             float2 v[16], Xa[16], Xb[16];
             forward_fft<L, NoHook, PSync>(segb, segb, e2, a.tw, v, Xa);
             forward_fft<L, NoHook, PSync>(segb + L, segb + L, e2, a.tw, v, Xb);
@@ -371,7 +407,10 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                     wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
                     if (t >= 2) wait_bar(&bar[B_MMA1 + (t - 2) % ND1], ((t - 2) / ND1) & 1, abort_flag);
                     __syncwarp();
-                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
+                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {
+                        nb_arrive(NB_A1 + (t & 1));
+                        continue;
+                    }
                     tmem_fence_after_sync();
                     const uint4 *hrow = reinterpret_cast<const uint4 *>(hb + slot * H_BYTES + k2 * H_ROW);
                     uint32_t y[32];
@@ -389,7 +428,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                     mbar_arrive(&bar[B_H_FREE + slot]);
                     tmem_st32(tmem_lane_addr(tmem, COL_A1 + 32 * (t & 1)), y);
                     tmem_fence_before_sync();
-                    mbar_arrive(&bar[B_A1_FULL + (t & 1)]);
+                    nb_arrive(NB_A1 + (t & 1));
                 }
             }
         }
@@ -410,7 +449,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         }
         uint32_t t = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const int grp = it % a.ng;
+            const int grp = src.item(it).grp;
             const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
             for (int zp = zp0; zp < zp1; ++zp) {
 #pragma unroll 1
@@ -419,7 +458,11 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                     wait_bar(&bar[B_MMA1 + t % ND1], (t / ND1) & 1, abort_flag);
                     if (zz == 0 && p >= 2) wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag);
                     __syncwarp();
-                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
+                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {
+                        nb_arrive(NB_D1 + t % ND1);
+                        if (zz == 1) nb_arrive(NB_B2 + (p & 1));
+                        continue;
+                    }
                     tmem_fence_after_sync();
                     unsigned char *base = b2 + (p & 1) * B2_BYTES + (size_t)(4 * sg + 8 * zz) * SBO2;
 #pragma unroll
@@ -428,7 +471,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                         tmem_ld32(tmem_lane_addr(tmem, COL_D1 + 64 * (t % ND1) + 32 * hh), d);
                         if (hh == 1) {
                             tmem_fence_before_sync();
-                            mbar_arrive(&bar[B_D1_FREE + t % ND1]);
+                            nb_arrive(NB_D1 + t % ND1);
                         }
                         uint32_t hr[8], hi[8];
 #pragma unroll
@@ -455,7 +498,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                     }
                     if (zz == 1) {
                         fence_proxy_async_smem();
-                        mbar_arrive(&bar[B_B2_FULL + (p & 1)]);
+                        nb_arrive(NB_B2 + (p & 1));
                     }
                 }
             }
@@ -469,31 +512,35 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         uint32_t p = 0;
         int il = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
-            const int sp = it / a.ng, grp = it % a.ng;
+            const Item ii = src.item(it);
+            const int sp = ii.sp, grp = ii.grp;
             const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
             wait_bar(&bar[B_SCALE0 + (il & 1)], (il >> 1) & 1, abort_flag);
             const float fs = scl[2 * (il & 1) + sq];
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_SFREE0 + (il & 1)]);
             // outputs kept in this segment: t in [0, lim) (the step S, cut at n; none past the launch)
-            const int64_t segrow = (int64_t)(a.seg_begin + 2 * sp + sq) * a.S;
-            const int64_t left = a.n - segrow;
-            const int lim = (2 * sp + sq < a.nseg && left > 0) ? (int)(left < a.S ? left : a.S) : 0;
+            const int64_t segrow = (int64_t)(ii.seg_begin + 2 * sp + sq) * a.S;
+            const int64_t left = ii.n - segrow;
+            const int lim = (2 * sp + sq < ii.nseg && left > 0) ? (int)(left < a.S ? left : a.S) : 0;
             const int tbase = lane - (a.K - 1);   // output index of n2 = 0
             for (int zp = zp0; zp < zp1; ++zp, ++p) {
                 wait_bar(&bar[B_MMA2 + (p & 1)], (p >> 1) & 1, abort_flag);
                 __syncwarp();
-                if (__shfl_sync(0xffffffffu, *abort_flag, 0)) continue;
+                if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {
+                    nb_arrive(NB_D2 + (p & 1));
+                    continue;
+                }
                 tmem_fence_after_sync();
                 const int z = 2 * zp + zq;
-                float *o = a.out + (size_t)z * (size_t)a.n + segrow;
+                float *o = ii.out + (size_t)z * (size_t)ii.n + segrow;
 #pragma unroll 1
                 for (int cc = 0; cc < 4; ++cc) {   // n2 = 16 cc .. 16 cc + 15
                     uint32_t r[32];
                     tmem_ld32(my + 128 * (p & 1) + 32 * cc, r);
                     if (cc == 3) {
                         tmem_fence_before_sync();
-                        mbar_arrive(&bar[B_D2_FREE + (p & 1)]);
+                        nb_arrive(NB_D2 + (p & 1));
                     }
                     if (z >= a.M) continue;
 #pragma unroll
@@ -509,18 +556,18 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             }
         }
     } else if (warp == 12) {
-        // ---------------- stage-1 MMA thread ----------------
-        if (lane == 0) {
-            const uint32_t b1a = smem_u32(sm + Smem::b1);
-            bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
-            uint32_t t = 0;
-            for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-                const int grp = it % a.ng;
-                const int ntiles = 2 * (a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng);
-                for (int j = 0; j < ntiles; ++j, ++t) {
-                    ok = ok && wait_bar(&bar[B_A1_FULL + (t & 1)], (t >> 1) & 1, abort_flag);
-                    if (t >= ND1) ok = ok && wait_bar(&bar[B_D1_FREE + t % ND1], ((t - ND1) / ND1) & 1, abort_flag);
-                    if (!ok) break;
+        // ---------------- stage-1 MMA warp (lane 0 issues) ----------------
+        const uint32_t b1a = smem_u32(sm + Smem::b1);
+        bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
+        __syncwarp();
+        uint32_t t = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const int grp = src.item(it).grp;
+            const int ntiles = 2 * (a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng);
+            for (int j = 0; j < ntiles; ++j, ++t) {
+                nb_sync(NB_A1 + (t & 1));                  // A1[t % 2] written
+                if (t >= ND1) nb_sync(NB_D1 + t % ND1);    // D1[t % 3] read by the twiddle group
+                if (lane == 0 && ok && !*abort_flag) {
                     tmem_fence_after_sync();
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
@@ -528,8 +575,10 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                                smem_desc(b1a + ks * 2 * LBO1, LBO1, SBO1), IDESC1, ks > 0);
                     mma_commit(&bar[B_MMA1 + t % ND1]);
                 }
+                __syncwarp();
             }
-            // no MMA may be in flight when the tensor memory is released
+        }
+        if (lane == 0) {   // no MMA may be in flight when the tensor memory is released
             for (uint32_t i = (t > ND1 ? t - ND1 : 0); i < t; ++i)
                 mbar_wait_bounded(&bar[B_MMA1 + i % ND1], (i / ND1) & 1, kWaitLimitNs);
             if (!ok || *abort_flag) {
@@ -538,18 +587,18 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             }
         }
     } else if (warp == 14) {
-        // ---------------- stage-2 MMA thread ----------------
-        if (lane == 0) {
-            const uint32_t b2a = smem_u32(b2), ga = smem_u32(sm + Smem::g);
-            bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
-            uint32_t q = 0;
-            for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-                const int grp = it % a.ng;
-                const int npairs = a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng;
-                for (int j = 0; j < npairs; ++j, ++q) {
-                    ok = ok && wait_bar(&bar[B_B2_FULL + (q & 1)], (q >> 1) & 1, abort_flag);
-                    if (q >= 2) ok = ok && wait_bar(&bar[B_D2_FREE + (q & 1)], ((q - 2) >> 1) & 1, abort_flag);
-                    if (!ok) break;
+        // ---------------- stage-2 MMA warp (lane 0 issues) ----------------
+        const uint32_t b2a = smem_u32(b2), ga = smem_u32(sm + Smem::g);
+        bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
+        __syncwarp();
+        uint32_t q = 0;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const int grp = src.item(it).grp;
+            const int npairs = a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng;
+            for (int j = 0; j < npairs; ++j, ++q) {
+                nb_sync(NB_B2 + (q & 1));                  // both tiles of pair q transposed
+                if (q >= 2) nb_sync(NB_D2 + (q & 1));      // D2[q % 2] read by the power group
+                if (lane == 0 && ok && !*abort_flag) {
                     tmem_fence_after_sync();
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks)
@@ -557,7 +606,10 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                                smem_desc(ga + ks * 2 * LBOG, LBOG, SBOG), IDESC2, ks > 0);
                     mma_commit(&bar[B_MMA2 + (q & 1)]);
                 }
+                __syncwarp();
             }
+        }
+        if (lane == 0) {
             for (uint32_t i = (q > 2 ? q - 2 : 0); i < q; ++i)
                 mbar_wait_bounded(&bar[B_MMA2 + (i & 1)], (i >> 1) & 1, kWaitLimitNs);
             if (!ok || *abort_flag) {
@@ -573,20 +625,20 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         uint32_t seg_issued = 0, tH = 0;
         bool ok = true;
         auto issue_segments = [&](int it) {
-            const int sp = it / a.ng;
+            const Item ii = src.item(it);
             mbar_arrive_expect_tx(&bar[B_SEG_FULL], 2u * L * (uint32_t)sizeof(float2));
 #pragma unroll 1
             for (int s2 = 0; s2 < 2; ++s2) {
-                const int c0 = (a.seg_begin + 2 * sp + s2) * a.S - (a.K - 1);
+                const int c0 = (ii.seg_begin + 2 * ii.sp + s2) * a.S - (a.K - 1);
 #pragma unroll
-                for (int j = 0; j < L / 256; ++j) tma_load_1d(segb + s2 * L + 256 * j, &tmap, c0 + 256 * j, &bar[B_SEG_FULL]);
+                for (int j = 0; j < L / 256; ++j) tma_load_1d(segb + s2 * L + 256 * j, ii.map, c0 + 256 * j, &bar[B_SEG_FULL]);
             }
             ++seg_issued;
         };
         if ((int)blockIdx.x < n_items) issue_segments(blockIdx.x);
         int il = 0;
         for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x, ++il) {
-            const int grp = it % a.ng;
+            const int grp = src.item(it).grp;
             const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
             const int ntiles = 2 * (zp1 - zp0);
             for (int j = 0; ok && j < ntiles; ++j, ++tH) {
@@ -616,6 +668,38 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     __syncthreads();
     tmem_fence_after_sync();
     if (warp == 12) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// One array: segments [s.seg_begin, s.seg_begin + s.nseg).
+__global__ void __launch_bounds__(tc2::kThreads, 1)
+    ols_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const tc2::Args a, const tc2::SingleSrc s0)
+{
+    tc2::SingleSrc src = s0;
+    src.map = &tmap;
+    tc2_body(src, a);
+}
+
+// Many arrays, one persistent launch: the same items and arithmetic per array as the
+// single-array kernel, so every plane is bit-identical to that array's fdas_convolve.
+// (Same parameter list as the FP32 batch kernel; the work counter is not used: items are
+// taken round-robin by block index.)
+__global__ void __launch_bounds__(tc2::kThreads, 1)
+    ols_tc2_batch(const __grid_constant__ BatchTable t, const OlsArgs o, int *counter)
+{
+    (void)counter;
+    tc2::Args a;
+    a.H16 = o.H16;
+    a.cst = o.cst;
+    a.tw = o.tw;
+    a.M = o.M;
+    a.S = o.S;
+    a.K = o.K;
+    a.ng = o.ng;
+    a.ZP = (o.M + 1) / 2;
+    a.eH = o.eH;
+    a.status = o.status;
+    const tc2::BatchSrc src{&t, o.ng};
+    tc2_body(src, a);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -659,8 +743,7 @@ static int tc2_groups(int64_t n_sp, int ZP, int sms)
     return best_ng;
 }
 
-cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsigned char *H16,
-                           const unsigned char *cst, int eH, int nseg, cudaStream_t s)
+static cudaError_t tc2_setup(int *sms_out)
 {
     static bool done[64] = {};
     static int sms[64] = {};
@@ -670,30 +753,63 @@ cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsi
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
         e = cudaFuncSetAttribute(ols_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ols_tc2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         done[dev] = true;
     }
+    *sms_out = sms[dev];
+    return cudaSuccess;
+}
+
+int tc2_groups_for(int64_t n_sp, int M)
+{
+    int sms = 0;
+    if (tc2_setup(&sms) != cudaSuccess || sms <= 0) sms = 1;
+    return tc2_groups(n_sp, (M + 1) / 2, sms);
+}
+
+cudaError_t tc2_batch_kernel(BatchKernel *k)
+{
+    int sms = 0;
+    cudaError_t e = tc2_setup(&sms);
+    if (e != cudaSuccess) return e;
+    k->fn = reinterpret_cast<const void *>(ols_tc2_batch);
+    k->block = tc2::kThreads;
+    k->smem = tc2::Smem::total;
+    k->resident = sms;   // one block per SM (tensor memory and shared memory)
+    return cudaSuccess;
+}
+
+cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsigned char *H16,
+                           const unsigned char *cst, int eH, int nseg, cudaStream_t s)
+{
+    int sms = 0;
+    cudaError_t e = tc2_setup(&sms);
+    if (e != cudaSuccess) return e;
     if (nseg <= 0) return cudaSuccess;
     tc2::Args a;
     a.H16 = H16;
     a.cst = cst;
     a.tw = o.tw;
-    a.out = o.out;
-    a.n = o.n;
     a.M = o.M;
     a.S = o.S;
     a.K = o.K;
-    a.seg_begin = o.seg_begin;
-    a.nseg = nseg;
-    a.n_sp = (nseg + 1) / 2;
     a.ZP = (o.M + 1) / 2;
-    a.ng = tc2_groups(a.n_sp, a.ZP, sms[dev]);
     a.eH = eH;
     a.status = o.status;
-    const int64_t items = (int64_t)a.n_sp * a.ng;
-    const int grid = (int)(items < sms[dev] ? items : sms[dev]);
-    ols_tc2_kernel<<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a);
+    tc2::SingleSrc src;
+    src.map = nullptr;   // the kernel points it at its own parameter copy of the map
+    src.out = o.out;
+    src.n = o.n;
+    src.seg_begin = o.seg_begin;
+    src.nseg = nseg;
+    src.n_sp = (nseg + 1) / 2;
+    a.ng = src.ng = tc2_groups(src.n_sp, a.ZP, sms);
+    const int64_t items = (int64_t)src.n_sp * src.ng;
+    const int grid = (int)(items < sms ? items : sms);
+    ols_tc2_kernel<<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     return cudaGetLastError();
 }
 

@@ -228,8 +228,8 @@ int fdas_server_create(fdas_server *out, fdas_plan plan, const fdas_server_opts 
     if (max_batch < 1 || max_batch > fdas::kBatchMax)
         return fdas::set_error(FDAS_ERR_INVALID_ARG, "max_batch outside [1, 120]");
     if (fdas::plan_grouped(plan)) return fdas::set_error(FDAS_ERR_UNSUPPORTED, "the server is built for ungrouped plans");
-    if (fdas::plan_precision(plan) != FDAS_PREC_FP32)
-        return fdas::set_error(FDAS_ERR_UNSUPPORTED, "the server is built for FP32 plans");
+    if (fdas::plan_precision(plan) == FDAS_PREC_TC_FP16)
+        return fdas::set_error(FDAS_ERR_UNSUPPORTED, "the server is not built for the single-pass tensor-core form");
     fdas_server_s *s = new (std::nothrow) fdas_server_s;
     if (!s) return fdas::set_error(FDAS_ERR_OOM, "host allocation");
     s->plan = plan;

@@ -37,14 +37,15 @@ class FdasError(RuntimeError):
 
 class fdas_opts(ctypes.Structure):
     _fields_ = [("seg_len", ctypes.c_int), ("tpl_per_cta", ctypes.c_int),
-                ("precision", ctypes.c_int), ("autotune", ctypes.c_int), ("group_support", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("autotune", ctypes.c_int), ("group_support", ctypes.c_int),
+                ("tune_n_min", ctypes.c_int64)]
 
 
 class fdas_plan_desc(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("n_templates", ctypes.c_int), ("tpl_len", ctypes.c_int),
                 ("frame_len", ctypes.c_int), ("seg_len", ctypes.c_int), ("seg_step", ctypes.c_int),
                 ("tpl_per_cta", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
-                ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 9),
+                ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_float * 12), ("tune_ms_tc", ctypes.c_float),
                 ("batch_blocks", ctypes.c_int), ("groups", ctypes.c_int)]
 
 
@@ -350,10 +351,11 @@ class Plan:
     """
 
     def __init__(self, templates, n_max: int, seg_len: int = 2048, tpl_per_cta: int = 0,
-                 precision: int = FDAS_PREC_FP32, autotune: int = 0, group_support: int = 0):
+                 precision: int = FDAS_PREC_FP32, autotune: int = 0, group_support: int = 0,
+                 tune_n_min: int = 0):
         t = np.ascontiguousarray(np.atleast_2d(templates), dtype=np.complex64)
         self.n_templates, self.tpl_len = t.shape
-        opts = fdas_opts(seg_len, tpl_per_cta, precision, autotune, group_support)
+        opts = fdas_opts(seg_len, tpl_per_cta, precision, autotune, group_support, tune_n_min)
         self.handle = fdas_plan_create(n_max, t.ctypes.data, self.n_templates, self.tpl_len, opts)
         self.desc = fdas_plan_describe(self.handle)
 

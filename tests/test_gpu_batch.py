@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity import TOL_FP32, compare
+from parity import TOL_FP32, TOL_TC, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -118,21 +118,44 @@ def test_repeated_batches_reuse_graph(fd, bank):
 
 
 def test_autotuner(fd, oracle_mod, bank):
-    with fd.Plan(bank, n_max=1 << 17, autotune=1) as plan:
+    # candidates (L, G) with G = 0 the per-call choice, timed on a proxy batch of 16 arrays with
+    # lengths log-uniform in [tune_n_min, n_max]
+    with fd.Plan(bank, n_max=1 << 17, autotune=1, tune_n_min=1 << 13) as plan:
         d = plan.desc
-        assert d.tuned == 1
-        assert d.seg_len in (1024, 2048, 4096) and d.tpl_per_cta in (5, 17, 85)
+        assert d.tuned == 1 and d.precision == fd.FDAS_PREC_FP32
+        assert d.seg_len in (1024, 2048, 4096) and d.tpl_per_cta in (0, 5, 17, 85)
         ms = np.array(d.tune_ms[:])
-        assert np.all(ms > 0)             # every candidate ran (K = 421 fits all three L)
-        idx = [1024, 2048, 4096].index(d.seg_len) * 3 + [5, 17, 85].index(d.tpl_per_cta)
+        assert np.all(ms > 0) and d.tune_ms_tc == 0   # every FP32 candidate ran, no tensor-core one
+        idx = [1024, 2048, 4096].index(d.seg_len) * 4 + [0, 5, 17, 85].index(d.tpl_per_cta)
         assert ms[idx] == ms.min()
         x = synth.make_input(synth.single_small(n=30000, seed=3))
         out = plan.convolve(torch.from_numpy(x).cuda())
         plan.status()
     compare(out.cpu().numpy(), oracle_mod.ols_power(x, bank), TOL_FP32)
     # a second plan with the same shape reuses the cached choice
-    with fd.Plan(bank, n_max=1 << 17, autotune=1) as plan2:
+    with fd.Plan(bank, n_max=1 << 17, autotune=1, tune_n_min=1 << 13) as plan2:
         assert (plan2.desc.seg_len, plan2.desc.tpl_per_cta) == (d.seg_len, d.tpl_per_cta)
+
+
+def test_autotuner_with_precision(fd, oracle_mod, bank):
+    # mode 2 adds the two-stage tensor-core form: whichever wins, the plan computes a correct
+    # plane at the tolerance of the chosen form, batched and single
+    with fd.Plan(bank, n_max=1 << 18, autotune=2) as plan:
+        d = plan.desc
+        assert d.tuned == 1 and d.tune_ms_tc > 0
+        best_fp32 = min(v for v in d.tune_ms[:] if v > 0)
+        if d.precision == fd.FDAS_PREC_TC_DFT2:
+            assert d.tune_ms_tc <= best_fp32 and d.seg_len == 2048
+        else:
+            assert d.precision == fd.FDAS_PREC_FP32 and best_fp32 <= d.tune_ms_tc
+        x = synth.make_input(synth.single_small(n=70000, seed=4))
+        xd = torch.from_numpy(x).cuda()
+        out = plan.convolve(xd)
+        outb = plan.convolve_batch([xd])[0]
+        plan.status()
+        assert torch.equal(out, outb)
+    tol = TOL_TC if d.precision == fd.FDAS_PREC_TC_DFT2 else TOL_FP32
+    compare(out.cpu().numpy(), oracle_mod.ols_power(x, bank), tol)
 
 
 @pytest.mark.slow

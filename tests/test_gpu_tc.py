@@ -120,13 +120,14 @@ def test_ska_array_vs_ols_oracle(fd, oracle_mod, bank, prec):
         assert p[m, i - 3:i + 4].max() > 20 * np.median(p[m])
 
 
-def test_batched_forms_reject_tensor_core_plans(fd, bank, prec):
-    # the batched, allocation-free and served entry points run the FP32 persistent kernel:
-    # a tensor-core plan is refused before anything is enqueued (the outputs keep their sentinel)
+def test_batched_forms_reject_the_single_pass_form(fd, bank):
+    # the batched, allocation-free and served entry points have no kernel for the single-pass
+    # tensor-core form: such a plan is refused before anything is enqueued (the outputs keep
+    # their sentinel)
     n = 5000
     x = torch.from_numpy((np.arange(n) % 7 - 3).astype(np.complex64)).cuda()
     out = torch.full((bank.shape[0], n), -1.0, dtype=torch.float32, device="cuda")
-    with fd.Plan(bank, n_max=n, precision=prec) as plan:
+    with fd.Plan(bank, n_max=n, precision=fd.FDAS_PREC_TC_FP16) as plan:
         for call in (fd.fdas_convolve_batch, fd.fdas_convolve_batch_noalloc):
             with pytest.raises(fd.FdasError) as e:
                 call(plan.handle, [x.data_ptr()], [n], [out.data_ptr()])
@@ -174,3 +175,55 @@ def test_dft2_template_counts(fd, oracle_mod, m):
     with fd.Plan(h, n_max=n, precision=fd.FDAS_PREC_TC_DFT2) as plan:
         p = _run(plan, x)
     compare(p, oracle_mod.direct_power(x, h), TOL_TC)
+
+
+def _rand_dev(n, seed):
+    rng = np.random.default_rng(seed)
+    return torch.from_numpy((rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)).cuda()
+
+
+def test_dft2_batch_noalloc_and_single_agree(fd, oracle_mod, bank):
+    # the persistent batch kernel of the two-stage form runs the same items and arithmetic per
+    # array as the single-array kernel: bit-identical planes, through the graph-replayed lane
+    # and through the allocation-free entry point
+    ns = [1, 5, 1627, 1628, 1629, 4000, 9001, 20011, 3, 65536, 300001]
+    xs = [_rand_dev(n, 900 + i) for i, n in enumerate(ns)]
+    with fd.Plan(bank, n_max=max(ns), precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        outs = plan.convolve_batch(xs)
+        singles = [plan.convolve(x) for x in xs]
+        na = [torch.full_like(o, -1.0) for o in outs]
+        for rep in range(2):
+            fd.fdas_convolve_batch_noalloc(plan.handle, [x.data_ptr() for x in xs], ns, [o.data_ptr() for o in na])
+            plan.status()
+            for o, s in zip(na, singles):
+                assert torch.equal(o, s)
+    for o, s in zip(outs, singles):
+        assert torch.equal(o, s)
+    for i in (2, 5, 7, 10):   # n >= K: the tolerance against max(P_ref) applies (see test_ragged_and_groups)
+        x = xs[i].cpu().numpy()
+        compare(outs[i].cpu().numpy(), oracle_mod.ols_power(x, bank), TOL_TC)
+
+
+def test_dft2_served_same_alone_and_in_the_mix(fd, oracle_mod, bank):
+    x_np = synth.make_input(synth.single_small(n=40000, seed=21))
+    x = torch.from_numpy(x_np).cuda()
+    with fd.Plan(bank, n_max=1 << 18, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        single = plan.convolve(x).clone()
+        with fd.Server(plan, budget_bytes=2 << 30, lanes=3, max_batch=8) as srv:
+            t = srv.submit(x)
+            alone = srv.wait(t, n=x.numel()).clone()
+            srv.release(t)
+            others = [_rand_dev(int(n), 700 + i) for i, n in enumerate(np.random.default_rng(6).integers(1, 1 << 18, 24))]
+            tickets = [srv.submit(o) for o in others[:12]]
+            tx = srv.submit(x)
+            tickets += [srv.submit(o) for o in others[12:]]
+            mixed = srv.wait(tx, n=x.numel()).clone()
+            srv.release(tx)
+            planes = [srv.wait(tk, n=o.numel()).clone() for tk, o in zip(tickets, others)]
+            for tk in tickets:
+                srv.release(tk)
+        plan.status()
+        assert torch.equal(alone, mixed) and torch.equal(alone, single)
+        for i in (0, 11, 23):
+            assert torch.equal(planes[i], plan.convolve(others[i]))
+    compare(mixed.cpu().numpy(), oracle_mod.ols_power(x_np, bank), TOL_TC)
