@@ -381,6 +381,7 @@ def run_fdas(args):
                  "length_sweep": bench_length_sweep(fd, dev, xd),
                  "batched": bench_batch(fd, h, dev), "served": bench_serve(fd, h, dev)}
 
+    link = host_link(dev) if rank == 0 and world == 1 and not args.no_e2e else None
     clock_summary = clocks.summary()
     sm_mhz = clock_summary.get("sm_mhz") or clock_summary.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -396,6 +397,13 @@ def run_fdas(args):
                 "plane_gbs": 4.0 * m * n * world / (ms_per_step / 1e3) / 1e9,
                 "model_tflops": model_flops(n, m, args.seg_len, h.shape[1]) * world / (ms_per_step / 1e3) / 1e12,
                 "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": cpu, "e2e": e2e,
+                "e2e_chain": ({"value": forms["candidates"]["e2e"]["arrays_per_s"], "unit": UNIT,
+                               "h2d_bytes_per_step": forms["candidates"]["e2e"]["h2d_bytes"],
+                               "d2h_bytes_per_step": forms["candidates"]["e2e"]["d2h_bytes"],
+                               "api": "plane -> threshold candidates -> host (fdas_convolve_candidates)"}
+                              if forms else None),
+                "host_link": link,
+                "roofline_tc": forms["tensor_core"]["tc_dft2"]["roofline"] if forms else None,
                 "clocks": clock_summary,
                 "forms": forms,
                 "gpu_launches": args.steps,
@@ -417,6 +425,24 @@ def _events_ms(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def host_link(dev, nbytes=1 << 30, reps=5):
+    """Pinned host <-> device copy rates (cudaMemcpyAsync through torch), GB/s: the ceiling of
+    any end-to-end rate that moves the plane to the host."""
+    import torch
+    hbuf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"bytes": nbytes, "api": "torch copy_ (cudaMemcpyAsync), pinned host buffer"}
+    for name, fn in (("h2d_gbs", lambda: dbuf.copy_(hbuf, non_blocking=True)),
+                     ("d2h_gbs", lambda: hbuf.copy_(dbuf, non_blocking=True))):
+        fn()
+        ms = _events_ms(fn, reps, stream)
+        out[name] = nbytes / (ms / 1e3) / 1e9
+    del hbuf, dbuf
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_tc(fd, h, dev, xd, reps=50):
     """Tensor-core form on the same array: radix-16 inverse passes as fp16 DFT-GEMMs
     (hi/lo DFT matrices, FP32 accumulation); beside it the FP32 kernel, same (L, G)."""
@@ -431,8 +457,17 @@ def bench_tc(fd, h, dev, xd, reps=50):
                 plan.convolve(xd, out, stream)
             ms = _events_ms(lambda: plan.convolve(xd, out, stream), reps, stream)
             plan.status(stream)
+        alg = algorithmic_bytes(n, m)
         res[name] = {"ms_per_array": ms, "arrays_per_s": 1e3 / ms,
-                     "hbm_frac": algorithmic_bytes(n, m) / (ms / 1e3) / 1e9 / measured_peaks()[0]}
+                     "hbm_frac": alg / (ms / 1e3) / 1e9 / measured_peaks()[0]}
+        if name == "tc_dft2":
+            peak, peak_kind = measured_peaks()
+            res[name]["roofline"] = {
+                "bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": alg / (ms / 1e3) / 1e9 / peak,
+                "traffic": profile_traffic("tc2") if n == 1 << 22 and m == 85 else None,
+                "peak_kind": peak_kind, "kernel": "ols_tc2_kernel", "algorithmic_bytes_per_launch": alg,
+                "avg_launch_ms": ms}
     res["accuracy"] = ("tests/test_gpu_tc.py: max |P - P_ref| / max P_ref < 1e-3 against the FP64 oracle "
                        "(tolerance 2e-3), strong-candidate sets identical")
     del out
