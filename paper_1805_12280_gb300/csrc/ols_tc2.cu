@@ -195,8 +195,9 @@ __device__ __forceinline__ bool p_all(bool ok)
 
 // Named hardware barriers for the handoffs between warps (a producer group of 128 threads
 // arrives, the consumer warp syncs): they wake the consumer far sooner than an mbarrier.
-// Every role runs its loops to the end, skipping work once the abort flag is set but still
-// arriving, so that no consumer waits on an arrival that never comes.
+// Every role runs its loops to the end, skipping a tile's work once one of its waits has given
+// up (a warp vote on the waits' results) but still arriving, so that no consumer waits on an
+// arrival that never comes.
 enum : int { NB_A1 = 2, NB_D1 = 4, NB_B2 = 7, NB_D2 = 9 };   // A1 x 2, D1 x 3, B2 x 2, D2 x 2
 constexpr int NB_COUNT = NT + 32;
 __device__ __forceinline__ void nb_arrive(int id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(NB_COUNT) : "memory"); }
@@ -404,10 +405,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
 #pragma unroll 1
                 for (int zz = 0; zz < 2; ++zz, ++t) {
                     const int slot = (int)(t % NH);
-                    wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
-                    if (t >= 2) wait_bar(&bar[B_MMA1 + (t - 2) % ND1], ((t - 2) / ND1) & 1, abort_flag);
-                    __syncwarp();
-                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {
+                    bool okw = wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
+                    if (t >= 2) okw = wait_bar(&bar[B_MMA1 + (t - 2) % ND1], ((t - 2) / ND1) & 1, abort_flag) && okw;
+                    if (!__all_sync(0xffffffffu, okw)) {
                         nb_arrive(NB_A1 + (t & 1));
                         continue;
                     }
@@ -455,30 +455,23 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
 #pragma unroll 1
                 for (int zz = 0; zz < 2; ++zz, ++t) {
                     const uint32_t p = t >> 1;
-                    wait_bar(&bar[B_MMA1 + t % ND1], (t / ND1) & 1, abort_flag);
-                    if (zz == 0 && p >= 2) wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag);
-                    __syncwarp();
-                    if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {
+                    bool okw = wait_bar(&bar[B_MMA1 + t % ND1], (t / ND1) & 1, abort_flag);
+                    if (zz == 0 && p >= 2) okw = wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag) && okw;
+                    if (!__all_sync(0xffffffffu, okw)) {
                         nb_arrive(NB_D1 + t % ND1);
                         if (zz == 1) nb_arrive(NB_B2 + (p & 1));
                         continue;
                     }
                     tmem_fence_after_sync();
                     unsigned char *base = b2 + (p & 1) * B2_BYTES + (size_t)(4 * sg + 8 * zz) * SBO2;
+                    const uint32_t dcol = tmem_lane_addr(tmem, COL_D1 + 64 * (t % ND1));
+                    auto chunk = [&](int j, const uint32_t (&d)[16]) {   // n1 = 8 j .. 8 j + 7
+                        uint32_t hr[4], hi[4];
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {   // n1 = 16 hh .. 16 hh + 15
-                        uint32_t d[32];
-                        tmem_ld32(tmem_lane_addr(tmem, COL_D1 + 64 * (t % ND1) + 32 * hh), d);
-                        if (hh == 1) {
-                            tmem_fence_before_sync();
-                            nb_arrive(NB_D1 + t % ND1);
-                        }
-                        uint32_t hr[8], hi[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {   // outputs n1 = 16 hh + 2q, +1
+                        for (int q = 0; q < 4; ++q) {   // outputs n1 = 8 j + 2 q, +1
                             const float2 re = make_float2(__uint_as_float(d[4 * q]), __uint_as_float(d[4 * q + 1]));
                             const float2 im = make_float2(__uint_as_float(d[4 * q + 2]), __uint_as_float(d[4 * q + 3]));
-                            const int w = 4 * (8 * hh + q);
+                            const int w = 4 * (4 * j + q);
                             const float2 tr = make_float2(tw[w], tw[w + 1]), ti = make_float2(tw[w + 2], tw[w + 3]);
                             const float2 zr = csub(pmul(re, tr), pmul(im, ti));
                             const float2 zi = pfma(re, ti, pmul(im, tr));
@@ -490,12 +483,25 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                             const int kap = 64 * ri + k2;
                             unsigned char *row = base + (kap >> 3) * LBO2 + (kap & 7) * 16;
                             const uint32_t *hv = ri ? hi : hr;
-#pragma unroll
-                            for (int c = 0; c < 2; ++c)   // n1 group of 8: 2 hh + c
-                                *reinterpret_cast<uint4 *>(row + (2 * hh + c) * SBO2) =
-                                    make_uint4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
+                            *reinterpret_cast<uint4 *>(row + j * SBO2) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         }
-                    }
+                    };
+                    // each chunk's arithmetic overlaps the next chunk's load; D1 is free once the last has landed
+                    uint32_t da[16], db[16];
+                    tmem_ld16_issue(dcol, da);
+                    tmem_ld16_wait(da);
+                    tmem_ld16_issue(dcol + 16, db);
+                    chunk(0, da);
+                    tmem_ld16_wait(db);
+                    tmem_ld16_issue(dcol + 32, da);
+                    chunk(1, db);
+                    tmem_ld16_wait(da);
+                    tmem_ld16_issue(dcol + 48, db);
+                    chunk(2, da);
+                    tmem_ld16_wait(db);
+                    tmem_fence_before_sync();
+                    nb_arrive(NB_D1 + t % ND1);
+                    chunk(3, db);
                     if (zz == 1) {
                         fence_proxy_async_smem();
                         nb_arrive(NB_B2 + (p & 1));
@@ -525,9 +531,8 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             const int lim = (2 * sp + sq < ii.nseg && left > 0) ? (int)(left < a.S ? left : a.S) : 0;
             const int tbase = lane - (a.K - 1);   // output index of n2 = 0
             for (int zp = zp0; zp < zp1; ++zp, ++p) {
-                wait_bar(&bar[B_MMA2 + (p & 1)], (p >> 1) & 1, abort_flag);
-                __syncwarp();
-                if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {
+                const bool okw = wait_bar(&bar[B_MMA2 + (p & 1)], (p >> 1) & 1, abort_flag);
+                if (!__all_sync(0xffffffffu, okw)) {
                     nb_arrive(NB_D2 + (p & 1));
                     continue;
                 }
@@ -543,14 +548,28 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                         nb_arrive(NB_D2 + (p & 1));
                     }
                     if (z >= a.M) continue;
+                    float2 pw[8];
 #pragma unroll
                     for (int g = 0; g < 8; ++g) {
                         const float2 re = make_float2(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]));
                         const float2 im = make_float2(__uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3]));
-                        const float2 pw = pmul(pfma(re, re, pmul(im, im)), make_float2(fs, fs));
-                        const int t0 = tbase + 32 * (16 * cc + 2 * g);
-                        if ((unsigned)t0 < (unsigned)lim) o[t0] = pw.x;
-                        if ((unsigned)(t0 + 32) < (unsigned)lim) o[t0 + 32] = pw.y;
+                        pw[g] = pmul(pfma(re, re, pmul(im, im)), make_float2(fs, fs));
+                    }
+                    const int c0 = 512 * cc - (a.K - 1);   // output of lane 0 at n2 = 16 cc (warp-uniform)
+                    if (c0 >= 0 && c0 + 511 < lim) {       // the whole chunk is kept: no per-store checks
+                        float *oc = o + (c0 + lane);
+#pragma unroll
+                        for (int g = 0; g < 8; ++g) {
+                            oc[64 * g] = pw[g].x;
+                            oc[64 * g + 32] = pw[g].y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int g = 0; g < 8; ++g) {
+                            const int t0 = tbase + 32 * (16 * cc + 2 * g);
+                            if ((unsigned)t0 < (unsigned)lim) o[t0] = pw[g].x;
+                            if ((unsigned)(t0 + 32) < (unsigned)lim) o[t0 + 32] = pw[g].y;
+                        }
                     }
                 }
             }
