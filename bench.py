@@ -497,48 +497,57 @@ def bench_groups(fd, h, dev, xd, reps=50):
 
 def bench_candidates(fd, h, dev, xd, x_host, reps=50, threshold=7.0):
     """Fused threshold epilogue (fdas_convolve_candidates): same array, the plane is never
-    written; end to end: pinned input -> device -> candidates -> host list."""
+    written; end to end: pinned input -> device -> candidates -> host list.  The FP32 form
+    (top-level keys) and the two-stage tensor-core form (`tensor_core`)."""
     import torch
     n = xd.numel()
     stream = torch.cuda.current_stream(dev)
-    res = {"workload": f"N=2^22, 85 templates, L=2048, G=85, threshold {threshold:g} (6 sigma)"}
-    with fd.Plan(h, n_max=n) as plan:
-        buf = torch.empty((1 << 22, 2), dtype=torch.int64, device=dev)
-        cnt = torch.empty(1, dtype=torch.int64, device=dev)
-        for _ in range(3):
-            plan.candidates(xd, threshold, buf.shape[0], stream, buf, cnt)
-        ms = _events_ms(lambda: plan.candidates(xd, threshold, buf.shape[0], stream, buf, cnt), reps, stream)
-        ncand = int(cnt.item())
-        res.update({"ms_per_array": ms, "arrays_per_s": 1e3 / ms, "candidates_per_array": ncand,
-                    "candidate_bytes": 16 * ncand})
-        xh = torch.from_numpy(x_host).pin_memory()
-        hbuf = torch.empty((buf.shape[0], 2), dtype=torch.int64).pin_memory()
-        hcnt = torch.empty(1, dtype=torch.int64).pin_memory()
-        xin = torch.empty_like(xd)
 
-        def e2e_step():
-            xin.copy_(xh, non_blocking=True)
-            plan.candidates(xin, threshold, buf.shape[0], stream, buf, cnt)
-            hcnt.copy_(cnt, non_blocking=False)
-            k = min(int(hcnt.item()), buf.shape[0])
-            hbuf[:k].copy_(buf[:k], non_blocking=False)
-        for _ in range(2):
-            e2e_step()
-        steps = 20
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            e2e_step()
-        dt = (time.perf_counter() - t0) / steps
-        plan.status(stream)
-        res["e2e"] = {"arrays_per_s": 1.0 / dt, "h2d_bytes": 8 * n, "d2h_bytes": 8 + 16 * ncand,
-                      "api": "fdas_convolve_candidates with pinned host input and candidate list"}
-        # the secondary set: the power whose exponential tail has the one-sided Gaussian 6-sigma
-        # probability, T_g = -ln Q(6)
-        tg = -math.log(0.5 * math.erfc(6.0 / math.sqrt(2.0)))
-        ms_g = _events_ms(lambda: plan.candidates(xd, tg, buf.shape[0], stream, buf, cnt), reps, stream)
-        res["gaussian_tail_threshold"] = {"threshold": tg, "ms_per_array": ms_g,
-                                          "candidates_per_array": int(cnt.item())}
-        plan.status(stream)
+    def run(precision, with_gauss):
+        out = {}
+        with fd.Plan(h, n_max=n, precision=precision) as plan:
+            buf = torch.empty((1 << 22, 2), dtype=torch.int64, device=dev)
+            cnt = torch.empty(1, dtype=torch.int64, device=dev)
+            for _ in range(3):
+                plan.candidates(xd, threshold, buf.shape[0], stream, buf, cnt)
+            ms = _events_ms(lambda: plan.candidates(xd, threshold, buf.shape[0], stream, buf, cnt), reps, stream)
+            ncand = int(cnt.item())
+            out.update({"ms_per_array": ms, "arrays_per_s": 1e3 / ms, "candidates_per_array": ncand,
+                        "candidate_bytes": 16 * ncand})
+            xh = torch.from_numpy(x_host).pin_memory()
+            hbuf = torch.empty((buf.shape[0], 2), dtype=torch.int64).pin_memory()
+            hcnt = torch.empty(1, dtype=torch.int64).pin_memory()
+            xin = torch.empty_like(xd)
+
+            def e2e_step():
+                xin.copy_(xh, non_blocking=True)
+                plan.candidates(xin, threshold, buf.shape[0], stream, buf, cnt)
+                hcnt.copy_(cnt, non_blocking=False)
+                k = min(int(hcnt.item()), buf.shape[0])
+                hbuf[:k].copy_(buf[:k], non_blocking=False)
+            for _ in range(2):
+                e2e_step()
+            steps = 20
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                e2e_step()
+            dt = (time.perf_counter() - t0) / steps
+            plan.status(stream)
+            out["e2e"] = {"arrays_per_s": 1.0 / dt, "h2d_bytes": 8 * n, "d2h_bytes": 8 + 16 * ncand,
+                          "api": "fdas_convolve_candidates with pinned host input and candidate list"}
+            if with_gauss:
+                # the secondary set: the power whose exponential tail has the one-sided Gaussian
+                # 6-sigma probability, T_g = -ln Q(6)
+                tg = -math.log(0.5 * math.erfc(6.0 / math.sqrt(2.0)))
+                ms_g = _events_ms(lambda: plan.candidates(xd, tg, buf.shape[0], stream, buf, cnt), reps, stream)
+                out["gaussian_tail_threshold"] = {"threshold": tg, "ms_per_array": ms_g,
+                                                  "candidates_per_array": int(cnt.item())}
+            plan.status(stream)
+        return out
+
+    res = {"workload": f"N=2^22, 85 templates, L=2048, G=85, threshold {threshold:g} (6 sigma)"}
+    res.update(run(fd.FDAS_PREC_FP32, True))
+    res["tensor_core"] = run(fd.FDAS_PREC_TC_DFT2, True)
     return res
 
 

@@ -170,8 +170,10 @@ typedef struct {
  *   count_dev  : device pointer to one unsigned 64-bit counter; the library clears it on
  *                `stream` before the launch; afterwards it holds the number of crossings
  *                found, which may exceed max_cand (then only max_cand were stored).
- * The order of the stored candidates is unspecified.  Asynchronous.  FP32 form only.
- * Errors: INVALID_ARG, UNSUPPORTED (tensor-core plan), CUDA.
+ * The order of the stored candidates is unspecified.  Asynchronous.  FP32 and two-stage
+ * tensor-core (FDAS_PREC_TC_DFT2) plans; for the latter the crossings and their powers are those
+ * of the plane that form writes, bit for bit.
+ * Errors: INVALID_ARG, UNSUPPORTED (an FDAS_PREC_TC_FP16 plan), CUDA.
  */
 int fdas_convolve_candidates(fdas_plan p, const void *in_c64_dev, int64_t n, float threshold,
                              fdas_candidate *cand_dev, int64_t max_cand,

@@ -924,7 +924,8 @@ int fdas_convolve_candidates(fdas_plan p, const void *in, int64_t n, float thres
     if (reinterpret_cast<uintptr_t>(in) % 16) return fail(FDAS_ERR_INVALID_ARG, "input pointer must be 16-byte aligned");
     if (reinterpret_cast<uintptr_t>(count) % 8 || reinterpret_cast<uintptr_t>(cand) % 8)
         return fail(FDAS_ERR_INVALID_ARG, "counter and candidate array must be 8-byte aligned");
-    if (p->precision != FDAS_PREC_FP32) return fail(FDAS_ERR_UNSUPPORTED, "candidates are built for the FP32 form");
+    if (p->precision == FDAS_PREC_TC_FP16)
+        return fail(FDAS_ERR_UNSUPPORTED, "candidates are built for the FP32 and two-stage tensor-core forms");
     DeviceGuard g(p->device);
     if (!g.ok) return fail(FDAS_ERR_CUDA, "cannot select plan device %d", p->device);
     CUtensorMap map;
@@ -937,6 +938,11 @@ int fdas_convolve_candidates(fdas_plan p, const void *in, int64_t n, float thres
     a.cand_count = count;
     a.cand_max = max_cand;
     a.threshold = threshold;
+    if (p->precision == FDAS_PREC_TC_DFT2) {
+        cudaError_t e = fdas::launch_ols_tc2(&map, a, p->d_H16, p->d_tc2c, p->eH, (int)n_segments(p, n), s);
+        if (e != cudaSuccess) return cuda_fail(e, "segment kernel launch (two-stage tensor-core form, candidates)");
+        return FDAS_OK;
+    }
     return launch_all(p, &map, a, n, s);
 }
 

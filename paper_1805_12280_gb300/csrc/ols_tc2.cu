@@ -47,6 +47,7 @@ namespace tc2 {
 constexpr int L = 2048, NT = 128;
 constexpr int kThreads = 3 * NT + 96;          // product, twiddle, power groups + 2 MMA warps + loader
 constexpr int NH = 4;                          // template buffers in flight
+constexpr int CAND_STAGE = 64;                 // threshold crossings staged per power warp
 constexpr uint32_t H_ROW = 144;                // bytes per k2 row of a template: 32 half2 + 16 B pad
 constexpr uint32_t H_BYTES = 64 * H_ROW;       // 9216 per template
 // B1 [N 64 x K 64] fp16, K-major, no swizzle: core matrices 8 rows x 16 B, K step LBO, row-group step SBO.
@@ -83,7 +84,8 @@ struct Smem {
     static constexpr size_t b1 = hb + NH * H_BYTES;
     static constexpr size_t g = b1 + B1_BYTES;                        // stage-2 DFT matrix
     static constexpr size_t b2 = g + G_BYTES;                         // 2 stage-2 operand buffers
-    static constexpr size_t red = b2 + 2 * B2_BYTES;                  // per-warp maxima [4][2]
+    static constexpr size_t stage = b2 + 2 * B2_BYTES;                // threshold epilogue: 64 records per power warp
+    static constexpr size_t red = stage + 4 * 64 * 16 + 16;           // per-warp maxima [4][2]
     static constexpr size_t scale = red + 8 * sizeof(float);          // [2 items][2 segments]
     static constexpr size_t bar = scale + 4 * sizeof(float);
     static constexpr size_t misc = bar + B_COUNT * 8;                 // TMEM address, abort flag
@@ -100,6 +102,11 @@ struct Args {
     int ng, ZP;                 // template-pair groups per segment pair, template pairs
     int eH;                     // template scale exponent
     int *status;
+    // threshold epilogue (fdas_convolve_candidates): crossings instead of the plane when cand != null
+    fdas_candidate *cand;
+    unsigned long long *cand_count;
+    long long cand_max;
+    float threshold;
 };
 
 // A work item: template-pair group `grp` of segment pair `sp` of one array.
@@ -293,7 +300,7 @@ __global__ void tc2_pretransform_kernel(const float2 *__restrict__ h32, int M, i
 // The segment kernel: one block per SM, work items (segment pair, template-pair range) taken
 // round-robin by block index.
 // ---------------------------------------------------------------------------------------
-template <class Src>
+template <bool CAND, class Src>
 __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
 {
     using namespace tc2;
@@ -515,6 +522,37 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         // the pair); columns 4 g + (0, 1, 2, 3) = re(2g), re(2g + 1), im(2g), im(2g + 1) of n2.
         const int q = warp & 3, sq = q & 1, zq = q >> 1;
         const uint32_t my = tmem_lane_addr(tmem, COL_D2);
+        // threshold epilogue: crossings staged per warp in shared memory (a shared counter per
+        // warp), one global reservation per flush; a full staging sends the excess straight out
+        fdas_candidate *stg = reinterpret_cast<fdas_candidate *>(sm + Smem::stage) + CAND_STAGE * q;
+        unsigned *scnt = reinterpret_cast<unsigned *>(sm + Smem::stage + 4 * CAND_STAGE * sizeof(fdas_candidate)) + q;
+        if (CAND && lane == 0) *scnt = 0;
+        __syncwarp();
+        auto put = [&](int tpl, float power, int64_t bin) {
+            fdas_candidate c;
+            c.tpl = tpl;
+            c.power = power;
+            c.bin = bin;
+            const unsigned k = atomicAdd(scnt, 1u);
+            if (k < (unsigned)CAND_STAGE) {
+                stg[k] = c;
+            } else {
+                const unsigned long long gi = atomicAdd(a.cand_count, 1ull);
+                if (gi < (unsigned long long)a.cand_max) a.cand[gi] = c;
+            }
+        };
+        auto flush_stage = [&]() {   // whole warp
+            __syncwarp();
+            const unsigned ns = min(*scnt, (unsigned)CAND_STAGE);
+            unsigned long long base = 0;
+            if (lane == 0 && ns > 0) base = atomicAdd(a.cand_count, (unsigned long long)ns);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (unsigned i = lane; i < ns; i += 32)
+                if (base + i < (unsigned long long)a.cand_max) a.cand[base + i] = stg[i];
+            __syncwarp();
+            if (lane == 0) *scnt = 0;
+            __syncwarp();
+        };
         uint32_t p = 0;
         int il = 0;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
@@ -555,6 +593,24 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                         const float2 im = make_float2(__uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3]));
                         pw[g] = pmul(pfma(re, re, pmul(im, im)), make_float2(fs, fs));
                     }
+                    if constexpr (CAND) {   // threshold epilogue: the kept outputs above the threshold, no plane
+                        float mx = fmaxf(pw[0].x, pw[0].y);
+#pragma unroll
+                        for (int g = 1; g < 8; ++g) mx = fmaxf(mx, fmaxf(pw[g].x, pw[g].y));
+                        if (!__any_sync(0xffffffffu, mx > a.threshold)) continue;   // most chunks: no crossing
+                        const int c0 = 512 * cc - (a.K - 1);
+                        const bool whole = c0 >= 0 && c0 + 511 < lim;   // every output of the chunk is kept
+#pragma unroll
+                        for (int g = 0; g < 8; ++g) {
+                            const int t0 = tbase + 32 * (16 * cc + 2 * g);
+                            const bool cx = pw[g].x > a.threshold && (whole || (unsigned)t0 < (unsigned)lim);
+                            const bool cy = pw[g].y > a.threshold && (whole || (unsigned)(t0 + 32) < (unsigned)lim);
+                            if (!__any_sync(0xffffffffu, cx || cy)) continue;
+                            if (cx) put(z, pw[g].x, segrow + t0);
+                            if (cy) put(z, pw[g].y, segrow + t0 + 32);
+                        }
+                        continue;
+                    }
                     const int c0 = 512 * cc - (a.K - 1);   // output of lane 0 at n2 = 16 cc (warp-uniform)
                     if (c0 >= 0 && c0 + 511 < lim) {       // the whole chunk is kept: no per-store checks
                         float *oc = o + (c0 + lane);
@@ -572,8 +628,13 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                         }
                     }
                 }
+                if constexpr (CAND) {
+                    __syncwarp();
+                    if (*scnt >= (unsigned)CAND_STAGE / 2) flush_stage();
+                }
             }
         }
+        if constexpr (CAND) flush_stage();
     } else if (warp == 12) {
         // ---------------- stage-1 MMA warp (lane 0 issues) ----------------
         const uint32_t b1a = smem_u32(sm + Smem::b1);
@@ -689,13 +750,15 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
     if (warp == 12) tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// One array: segments [s.seg_begin, s.seg_begin + s.nseg).
+// One array: segments [s.seg_begin, s.seg_begin + s.nseg); CAND: the threshold crossings
+// instead of the plane (a separate instantiation, so the plane kernel carries none of it).
+template <bool CAND>
 __global__ void __launch_bounds__(tc2::kThreads, 1)
     ols_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const tc2::Args a, const tc2::SingleSrc s0)
 {
     tc2::SingleSrc src = s0;
     src.map = &tmap;
-    tc2_body(src, a);
+    tc2_body<CAND>(src, a);
 }
 
 // Many arrays, one persistent launch: the same items and arithmetic per array as the
@@ -717,8 +780,12 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     a.ZP = (o.M + 1) / 2;
     a.eH = o.eH;
     a.status = o.status;
+    a.cand = nullptr;
+    a.cand_count = nullptr;
+    a.cand_max = 0;
+    a.threshold = 0.f;
     const tc2::BatchSrc src{&t, o.ng};
-    tc2_body(src, a);
+    tc2_body<false>(src, a);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -771,7 +838,9 @@ static cudaError_t tc2_setup(int *sms_out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
-        e = cudaFuncSetAttribute(ols_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
+        e = cudaFuncSetAttribute(ols_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ols_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(ols_tc2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
@@ -818,6 +887,10 @@ cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsi
     a.ZP = (o.M + 1) / 2;
     a.eH = eH;
     a.status = o.status;
+    a.cand = o.cand;
+    a.cand_count = o.cand_count;
+    a.cand_max = o.cand_max;
+    a.threshold = o.threshold;
     tc2::SingleSrc src;
     src.map = nullptr;   // the kernel points it at its own parameter copy of the map
     src.out = o.out;
@@ -828,7 +901,8 @@ cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsi
     a.ng = src.ng = tc2_groups(src.n_sp, a.ZP, sms);
     const int64_t items = (int64_t)src.n_sp * src.ng;
     const int grid = (int)(items < sms ? items : sms);
-    ols_tc2_kernel<<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
+    if (a.cand) ols_tc2_kernel<true><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
+    else ols_tc2_kernel<false><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     return cudaGetLastError();
 }
 

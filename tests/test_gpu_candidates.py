@@ -128,3 +128,39 @@ def test_candidates_past_the_block_staging(fd, bank, threshold):
     np.testing.assert_array_equal(got["tpl"], zi)
     np.testing.assert_array_equal(got["bin"], ii)
     np.testing.assert_array_equal(got["power"], plane[zi, ii])
+
+
+@pytest.mark.parametrize("n,threshold", [(1 << 14, THRESHOLD), (9001, THRESHOLD), (1, THRESHOLD), (20000, 0.5),
+                                         (3000, -1.0), (1 << 20, THRESHOLD)])
+def test_two_stage_candidates_equal_its_thresholded_plane(fd, bank, n, threshold):
+    # the two-stage tensor-core form's threshold epilogue: the same crossings, with the same
+    # powers bit for bit, as thresholding the plane that form writes (T < 0: every output)
+    x = synth.make_input(synth.single_small(n=max(n, 2), seed=35))[:n]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    with fd.Plan(bank, n_max=max(n, 16), precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        plane = plan.convolve(xd).cpu().numpy()
+        buf, count = plan.candidates(xd, threshold=threshold, max_cand=85 * n + 16)
+        plan.status()
+        got = _keys(fd.candidates_to_numpy(buf, count))
+    zi, ii = np.nonzero(plane > threshold)
+    assert int(count.item()) == zi.size and (threshold > 0 or zi.size == 85 * n)
+    np.testing.assert_array_equal(got["tpl"], zi)
+    np.testing.assert_array_equal(got["bin"], ii)
+    np.testing.assert_array_equal(got["power"], plane[zi, ii])
+
+
+def test_two_stage_candidates_truncation(fd, bank):
+    n = 30011
+    xd = torch.from_numpy(synth.make_input(synth.single_small(n=n, seed=36))).cuda()
+    with fd.Plan(bank, n_max=n, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        full_buf, full_count = plan.candidates(xd, threshold=3.0, max_cand=85 * n)
+        total = int(full_count.item())
+        assert total > 100
+        buf, count = plan.candidates(xd, threshold=3.0, max_cand=10)    # counts everything, stores 10
+        assert int(count.item()) == total
+        part = fd.candidates_to_numpy(buf, count)
+        full = fd.candidates_to_numpy(full_buf, full_count)
+        assert part.size == 10 and set(zip(part["tpl"], part["bin"])) <= set(zip(full["tpl"], full["bin"]))
+        _, count0 = plan.candidates(xd, threshold=3.0, max_cand=0)      # counting only
+        assert int(count0.item()) == total
+        plan.status()
