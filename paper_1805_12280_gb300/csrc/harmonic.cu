@@ -166,6 +166,9 @@ __global__ void __launch_bounds__(kHsThreads, 2) harmonic_kernel_narrow(const fl
     __shared__ fdas_harmonic_candidate stage[kHsThreads / 32][kWarpStage];
     __shared__ unsigned n_staged[kHsThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the next run of rows reads the same plane and appends to the same list: nothing here
+    // feeds it, so it may start as soon as this launch's blocks leave room
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (lane == 0) n_staged[warp] = 0;
     __syncwarp();
     const int c = (m - 1) / 2;
@@ -265,9 +268,21 @@ cudaError_t launch_hs(int H, const float *P, int m, int64_t n, int64_t bin0, con
             const int64_t tiles_per_row = (rmax + tile - 1) / tile;
             if ((e = resident_grid((const void *)fn, (int64_t)(y1 - y0) * tiles_per_row, &grid)) != cudaSuccess)
                 return e;
-            fn<<<grid, kHsThreads, 0, s>>>(P, m, (int)n, (int)bin0, y0, y1 - y0, (int)tiles_per_row, thr, lim, out,
-                                           max_cand, count);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            // launches after the first may overlap the one before (programmatic dependent launch):
+            // the runs are independent, and the tail of one run fills with the next
+            cudaLaunchAttribute attr{};
+            attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr.val.programmaticStreamSerializationAllowed = 1;
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(kHsThreads);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = s;
+            cfg.attrs = &attr;
+            cfg.numAttrs = y0 > 0 ? 1 : 0;
+            if ((e = cudaLaunchKernelEx(&cfg, fn, P, m, (int)n, (int)bin0, y0, y1 - y0, (int)tiles_per_row, thr, lim, out,
+                                        max_cand, count)) != cudaSuccess)
+                return e;
             y0 = y1;
         }
         return cudaSuccess;
