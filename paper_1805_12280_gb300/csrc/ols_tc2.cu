@@ -85,7 +85,7 @@ struct Smem {
     static constexpr size_t g = b1 + B1_BYTES;                        // stage-2 DFT matrix
     static constexpr size_t b2 = g + G_BYTES;                         // 2 stage-2 operand buffers
     static constexpr size_t stage = b2 + 2 * B2_BYTES;                // threshold epilogue: 64 records per power warp
-    static constexpr size_t red = stage + 4 * 64 * 16 + 16;           // per-warp maxima [4][2]
+    static constexpr size_t red = stage + 4 * 64 * 16;                // per-warp maxima [4][2]
     static constexpr size_t scale = red + 8 * sizeof(float);          // [2 items][2 segments]
     static constexpr size_t bar = scale + 4 * sizeof(float);
     static constexpr size_t misc = bar + B_COUNT * 8;                 // TMEM address, abort flag
@@ -522,36 +522,20 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         // the pair); columns 4 g + (0, 1, 2, 3) = re(2g), re(2g + 1), im(2g), im(2g + 1) of n2.
         const int q = warp & 3, sq = q & 1, zq = q >> 1;
         const uint32_t my = tmem_lane_addr(tmem, COL_D2);
-        // threshold epilogue: crossings staged per warp in shared memory (a shared counter per
-        // warp), one global reservation per flush; a full staging sends the excess straight out
+        // threshold epilogue: crossings staged per warp in shared memory at slots given by warp
+        // ballots (no atomics), one global reservation per flush of the staging
         fdas_candidate *stg = reinterpret_cast<fdas_candidate *>(sm + Smem::stage) + CAND_STAGE * q;
-        unsigned *scnt = reinterpret_cast<unsigned *>(sm + Smem::stage + 4 * CAND_STAGE * sizeof(fdas_candidate)) + q;
-        if (CAND && lane == 0) *scnt = 0;
-        __syncwarp();
-        auto put = [&](int tpl, float power, int64_t bin) {
-            fdas_candidate c;
-            c.tpl = tpl;
-            c.power = power;
-            c.bin = bin;
-            const unsigned k = atomicAdd(scnt, 1u);
-            if (k < (unsigned)CAND_STAGE) {
-                stg[k] = c;
-            } else {
-                const unsigned long long gi = atomicAdd(a.cand_count, 1ull);
-                if (gi < (unsigned long long)a.cand_max) a.cand[gi] = c;
-            }
-        };
+        unsigned nst = 0;   // staged records (warp-uniform)
+        const unsigned lt = (1u << lane) - 1u;
         auto flush_stage = [&]() {   // whole warp
             __syncwarp();
-            const unsigned ns = min(*scnt, (unsigned)CAND_STAGE);
             unsigned long long base = 0;
-            if (lane == 0 && ns > 0) base = atomicAdd(a.cand_count, (unsigned long long)ns);
+            if (lane == 0 && nst > 0) base = atomicAdd(a.cand_count, (unsigned long long)nst);
             base = __shfl_sync(0xffffffffu, base, 0);
-            for (unsigned i = lane; i < ns; i += 32)
+            for (unsigned i = lane; i < nst; i += 32)
                 if (base + i < (unsigned long long)a.cand_max) a.cand[base + i] = stg[i];
             __syncwarp();
-            if (lane == 0) *scnt = 0;
-            __syncwarp();
+            nst = 0;
         };
         uint32_t p = 0;
         int il = 0;
@@ -605,9 +589,25 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                             const int t0 = tbase + 32 * (16 * cc + 2 * g);
                             const bool cx = pw[g].x > a.threshold && (whole || (unsigned)t0 < (unsigned)lim);
                             const bool cy = pw[g].y > a.threshold && (whole || (unsigned)(t0 + 32) < (unsigned)lim);
-                            if (!__any_sync(0xffffffffu, cx || cy)) continue;
-                            if (cx) put(z, pw[g].x, segrow + t0);
-                            if (cy) put(z, pw[g].y, segrow + t0 + 32);
+                            const unsigned bx = __ballot_sync(0xffffffffu, cx), by = __ballot_sync(0xffffffffu, cy);
+                            if ((bx | by) == 0) continue;
+                            const unsigned nx = __popc(bx), nxy = nx + __popc(by);
+                            if (nst + nxy > (unsigned)CAND_STAGE) flush_stage();
+                            if (cx) {
+                                fdas_candidate c;
+                                c.tpl = z;
+                                c.power = pw[g].x;
+                                c.bin = segrow + t0;
+                                stg[nst + __popc(bx & lt)] = c;
+                            }
+                            if (cy) {
+                                fdas_candidate c;
+                                c.tpl = z;
+                                c.power = pw[g].y;
+                                c.bin = segrow + t0 + 32;
+                                stg[nst + nx + __popc(by & lt)] = c;
+                            }
+                            nst += nxy;
                         }
                         continue;
                     }
@@ -628,10 +628,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                         }
                     }
                 }
-                if constexpr (CAND) {
-                    __syncwarp();
-                    if (*scnt >= (unsigned)CAND_STAGE / 2) flush_stage();
-                }
+
             }
         }
         if constexpr (CAND) flush_stage();
