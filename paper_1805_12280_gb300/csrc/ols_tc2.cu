@@ -409,7 +409,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             }
             mbar_arrive(&bar[B_SEG_FREE]);
             for (int zp = zp0; zp < zp1; ++zp) {
-#pragma unroll 1
+#pragma unroll
                 for (int zz = 0; zz < 2; ++zz, ++t) {
                     const int slot = (int)(t % NH);
                     bool okw = wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
