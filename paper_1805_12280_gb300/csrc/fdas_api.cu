@@ -568,9 +568,9 @@ static int fill_batch(fdas_plan p, BatchTable &t, OlsArgs &a, int first, int cnt
         a.H16 = p->d_H16;
         a.cst = p->d_tc2c;
         a.eH = p->eH;
-        a.ng = tc2_groups_for(units, p->M);
+        a.ng = 1;   // the kernel shares the launch's (segment pair, template pair) units out evenly
         a.G = p->M;
-        per_unit = a.ng;
+        per_unit = 1;
     } else {
         a.G = call_G(p, units, p->M);
         per_unit = (p->M + a.G - 1) / a.G;
@@ -586,6 +586,8 @@ static int fill_batch(fdas_plan p, BatchTable &t, OlsArgs &a, int first, int cnt
         ar.item_off = items;
         items += (int64_t)(tc2 ? (ar.nseg + 1) / 2 : ar.nseg) * per_unit;
     }
+    if (tc2 && items * ((p->M + 1) / 2) >= ((int64_t)1 << 31))   // the kernel counts units in 32 bits
+        return fail(FDAS_ERR_INVALID_ARG, "batch too large for one launch of the tensor-core form");
     t.count = cnt;
     t.total_items = items;
     return FDAS_OK;

@@ -109,39 +109,80 @@ struct Args {
     float threshold;
 };
 
-// A work item: template-pair group `grp` of segment pair `sp` of one array.
+// A work item: template pairs [zp0, zp1) of segment pair `sp` of one array.
 struct Item {
     const CUtensorMap *map;     // the array's input tensor map
     float *out;                 // its plane [M][n]
     int64_t n;
     int seg_begin, nseg;        // the segments [seg_begin, seg_begin + nseg) this launch covers
-    int sp, grp;
+    int sp, zp0, zp1;
 };
-// One array (fdas_convolve): items (sp, grp) in order, sp = it / ng.
+// One array (fdas_convolve): the n_sp x ZP (segment pair, template pair) units in order, an
+// equal share per block (q units, one more for the first r blocks), cut into items at
+// segment-pair boundaries; a segment pair split between two blocks has its forward FFTs done
+// by both.  The unit count fits 32 bits (the launcher checks it).
 struct SingleSrc {
     const CUtensorMap *map;
     float *out;
     int64_t n;
-    int seg_begin, nseg, n_sp, ng;
-    __device__ __forceinline__ int count() const { return n_sp * ng; }
-    __device__ __forceinline__ Item item(int it) const { return Item{map, out, n, seg_begin, nseg, it / ng, it % ng}; }
+    int seg_begin, nseg, n_sp, ZP;
+    int q, r;
+    __device__ __forceinline__ unsigned u0() const
+    {
+        const unsigned b = blockIdx.x;
+        return b * (unsigned)q + (b < (unsigned)r ? b : (unsigned)r);
+    }
+    __device__ __forceinline__ unsigned u1() const { return u0() + (unsigned)q + (blockIdx.x < (unsigned)r ? 1u : 0u); }
+    __device__ __forceinline__ int count() const
+    {
+        const unsigned a0 = u0(), a1 = u1();
+        return a1 > a0 ? (int)((a1 - 1) / (unsigned)ZP - a0 / (unsigned)ZP + 1) : 0;
+    }
+    __device__ __forceinline__ Item item(int k) const
+    {
+        const unsigned a0 = u0(), a1 = u1();
+        const int sp = (int)(a0 / (unsigned)ZP) + k;
+        const unsigned b0 = (unsigned)sp * (unsigned)ZP, e0 = b0 + (unsigned)ZP;
+        const int zp0 = (int)((a0 > b0 ? a0 : b0) - b0), zp1 = (int)((a1 < e0 ? a1 : e0) - b0);
+        return Item{map, out, n, seg_begin, nseg, sp, zp0, zp1};
+    }
 };
-// Many arrays (fdas_convolve_batch): array i owns items [item_off_i, item_off_i + n_sp_i ng).
+// Many arrays (fdas_convolve_batch): array i owns segment pairs [item_off_i, item_off_i +
+// n_sp_i) of the launch; the units (segment pair, template pair) of all arrays in order are
+// shared out like those of one array, items cut at segment-pair (so also array) boundaries.
 struct BatchSrc {
     const BatchTable *t;
-    int ng;
-    __device__ __forceinline__ int count() const { return (int)t->total_items; }
-    __device__ __forceinline__ Item item(int it) const
+    int ZP;
+    __device__ __forceinline__ unsigned units() const { return (unsigned)t->total_items * (unsigned)ZP; }
+    __device__ __forceinline__ unsigned u0() const
     {
-        int lo = 0, hi = t->count - 1;   // the last array whose first item is <= it
+        const unsigned U = units(), b = blockIdx.x, q = U / gridDim.x, r = U % gridDim.x;
+        return b * q + (b < r ? b : r);
+    }
+    __device__ __forceinline__ unsigned u1() const
+    {
+        const unsigned U = units(), b = blockIdx.x, q = U / gridDim.x, r = U % gridDim.x;
+        return b * q + (b < r ? b : r) + q + (b < r ? 1u : 0u);
+    }
+    __device__ __forceinline__ int count() const
+    {
+        const unsigned a0 = u0(), a1 = u1();
+        return a1 > a0 ? (int)((a1 - 1) / (unsigned)ZP - a0 / (unsigned)ZP + 1) : 0;
+    }
+    __device__ __forceinline__ Item item(int k) const
+    {
+        const unsigned a0 = u0(), a1 = u1();
+        const int gsp = (int)(a0 / (unsigned)ZP) + k;
+        int lo = 0, hi = t->count - 1;   // the last array whose first segment pair is <= gsp
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (t->arr[mid].item_off <= it) lo = mid;
+            if (t->arr[mid].item_off <= gsp) lo = mid;
             else hi = mid - 1;
         }
-        const BatchArray &b = t->arr[lo];
-        const int local = it - (int)b.item_off;
-        return Item{&b.map, b.out, b.n, 0, b.nseg, local / ng, local % ng};
+        const BatchArray &ba = t->arr[lo];
+        const unsigned b0 = (unsigned)gsp * (unsigned)ZP, e0 = b0 + (unsigned)ZP;
+        const int zp0 = (int)((a0 > b0 ? a0 : b0) - b0), zp1 = (int)((a1 < e0 ? a1 : e0) - b0);
+        return Item{&ba.map, ba.out, ba.n, 0, ba.nseg, gsp - (int)ba.item_off, zp0, zp1};
     }
 };
 
@@ -317,7 +358,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Smem::misc + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_items = src.count();
+    const int nk = src.count();   // this block's items
     constexpr int CTRL = 3 * NT;   // the MMA thread initialises the barriers
 
     if (tid == CTRL) {
@@ -349,9 +390,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         const int k2 = tid & 63, sg = tid >> 6;
         uint32_t t = 0;
         int il = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
-            const int grp = src.item(it).grp;
-            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+        for (int k = 0; k < nk; ++k, ++il) {
+            const Item ii = src.item(k);
+            const int zp0 = ii.zp0, zp1 = ii.zp1;
             if (!p_all(!*abort_flag && wait_bar(&bar[B_SEG_FULL], il & 1, abort_flag))) {
                 for (int j = 0; j < 2 * (zp1 - zp0); ++j, ++t) nb_arrive(NB_A1 + (t & 1));   // keep the handoffs
                 continue;
@@ -455,9 +496,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             }
         }
         uint32_t t = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const int grp = src.item(it).grp;
-            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+        for (int k = 0; k < nk; ++k) {
+            const Item ii = src.item(k);
+            const int zp0 = ii.zp0, zp1 = ii.zp1;
             for (int zp = zp0; zp < zp1; ++zp) {
 #pragma unroll 1
                 for (int zz = 0; zz < 2; ++zz, ++t) {
@@ -539,10 +580,10 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         };
         uint32_t p = 0;
         int il = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++il) {
-            const Item ii = src.item(it);
-            const int sp = ii.sp, grp = ii.grp;
-            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+        for (int k = 0; k < nk; ++k, ++il) {
+            const Item ii = src.item(k);
+            const int sp = ii.sp;
+            const int zp0 = ii.zp0, zp1 = ii.zp1;
             wait_bar(&bar[B_SCALE0 + (il & 1)], (il >> 1) & 1, abort_flag);
             const float fs = scl[2 * (il & 1) + sq];
             __syncwarp();
@@ -638,9 +679,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
         __syncwarp();
         uint32_t t = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const int grp = src.item(it).grp;
-            const int ntiles = 2 * (a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng);
+        for (int k = 0; k < nk; ++k) {
+            const Item ii = src.item(k);
+            const int ntiles = 2 * (ii.zp1 - ii.zp0);
             for (int j = 0; j < ntiles; ++j, ++t) {
                 nb_sync(NB_A1 + (t & 1));                  // A1[t % 2] written
                 if (t >= ND1) nb_sync(NB_D1 + t % ND1);    // D1[t % 3] read by the twiddle group
@@ -669,9 +710,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         bool ok = wait_bar(&bar[B_B1_FULL], 0, abort_flag);
         __syncwarp();
         uint32_t q = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const int grp = src.item(it).grp;
-            const int npairs = a.ZP * (grp + 1) / a.ng - a.ZP * grp / a.ng;
+        for (int k = 0; k < nk; ++k) {
+            const Item ii = src.item(k);
+            const int npairs = ii.zp1 - ii.zp0;
             for (int j = 0; j < npairs; ++j, ++q) {
                 nb_sync(NB_B2 + (q & 1));                  // both tiles of pair q transposed
                 if (q >= 2) nb_sync(NB_D2 + (q & 1));      // D2[q % 2] read by the power group
@@ -701,8 +742,8 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         bulk_load(sm + Smem::g, a.cst + CB_G, G_BYTES, &bar[B_B1_FULL]);
         uint32_t seg_issued = 0, tH = 0;
         bool ok = true;
-        auto issue_segments = [&](int it) {
-            const Item ii = src.item(it);
+        auto issue_segments = [&](int k) {
+            const Item ii = src.item(k);
             mbar_arrive_expect_tx(&bar[B_SEG_FULL], 2u * L * (uint32_t)sizeof(float2));
 #pragma unroll 1
             for (int s2 = 0; s2 < 2; ++s2) {
@@ -712,11 +753,11 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             }
             ++seg_issued;
         };
-        if ((int)blockIdx.x < n_items) issue_segments(blockIdx.x);
+        if (nk > 0) issue_segments(0);
         int il = 0;
-        for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x, ++il) {
-            const int grp = src.item(it).grp;
-            const int zp0 = a.ZP * grp / a.ng, zp1 = a.ZP * (grp + 1) / a.ng;
+        for (int k = 0; ok && k < nk; ++k, ++il) {
+            const Item ii = src.item(k);
+            const int zp0 = ii.zp0, zp1 = ii.zp1;
             const int ntiles = 2 * (zp1 - zp0);
             for (int j = 0; ok && j < ntiles; ++j, ++tH) {
                 const uint32_t slot = tH % NH;
@@ -725,9 +766,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                 mbar_arrive_expect_tx(&bar[B_H_FULL + slot], H_BYTES);
                 bulk_load(hb + slot * H_BYTES, a.H16 + (size_t)(2 * zp0 + j) * H_BYTES, H_BYTES, &bar[B_H_FULL + slot]);
                 // once the product group has taken this item's spectra, fetch the next item's segments
-                if (j == min(NH, ntiles) - 1 && it + (int)gridDim.x < n_items) {
+                if (j == min(NH, ntiles) - 1 && k + 1 < nk) {
                     ok = wait_bar(&bar[B_SEG_FREE], il & 1, abort_flag);
-                    if (ok) issue_segments(it + gridDim.x);
+                    if (ok) issue_segments(k + 1);
                 }
             }
         }
@@ -781,7 +822,9 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     a.cand_count = nullptr;
     a.cand_max = 0;
     a.threshold = 0.f;
-    const tc2::BatchSrc src{&t, o.ng};
+    tc2::BatchSrc src;
+    src.t = &t;
+    src.ZP = a.ZP;
     tc2_body<false>(src, a);
 }
 
@@ -895,9 +938,13 @@ cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsi
     src.seg_begin = o.seg_begin;
     src.nseg = nseg;
     src.n_sp = (nseg + 1) / 2;
-    a.ng = src.ng = tc2_groups(src.n_sp, a.ZP, sms);
-    const int64_t items = (int64_t)src.n_sp * src.ng;
-    const int grid = (int)(items < sms ? items : sms);
+    src.ZP = a.ZP;
+    a.ng = 1;   // not used: the blocks split the (segment pair, template pair) units evenly
+    const int64_t units = (int64_t)src.n_sp * a.ZP;
+    if (units >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    const int grid = (int)(units < sms ? units : sms);
+    src.q = (int)(units / grid);
+    src.r = (int)(units % grid);
     if (a.cand) ols_tc2_kernel<true><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     else ols_tc2_kernel<false><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     return cudaGetLastError();
