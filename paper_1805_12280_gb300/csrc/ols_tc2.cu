@@ -117,16 +117,18 @@ struct Item {
     int seg_begin, nseg;        // the segments [seg_begin, seg_begin + nseg) this launch covers
     int sp, zp0, zp1;
 };
-// One array (fdas_convolve): the n_sp x ZP (segment pair, template pair) units in order, an
-// equal share per block (q units, one more for the first r blocks), cut into items at
-// segment-pair boundaries; a segment pair split between two blocks has its forward FFTs done
-// by both.  The unit count fits 32 bits (the launcher checks it).
+// One array (fdas_convolve).  ng = 0: the n_sp x ZP (segment pair, template pair) units in
+// order, an equal share per block (q units, one more for the first r blocks), cut into items
+// at segment-pair boundaries; a segment pair split between two blocks has its forward FFTs
+// done by both (the unit count fits 32 bits: the launcher checks it).  ng > 0 (short arrays,
+// a few units per block): items (segment pair, one of ng template-pair groups) in turn by
+// block, so that no block crosses a segment pair.
 struct SingleSrc {
     const CUtensorMap *map;
     float *out;
     int64_t n;
     int seg_begin, nseg, n_sp, ZP;
-    int q, r;
+    int q, r, ng;
     __device__ __forceinline__ unsigned u0() const
     {
         const unsigned b = blockIdx.x;
@@ -135,11 +137,19 @@ struct SingleSrc {
     __device__ __forceinline__ unsigned u1() const { return u0() + (unsigned)q + (blockIdx.x < (unsigned)r ? 1u : 0u); }
     __device__ __forceinline__ int count() const
     {
+        if (ng > 0) {
+            const unsigned items = (unsigned)n_sp * (unsigned)ng, b = blockIdx.x;
+            return b < items ? (int)((items - 1 - b) / gridDim.x + 1) : 0;
+        }
         const unsigned a0 = u0(), a1 = u1();
         return a1 > a0 ? (int)((a1 - 1) / (unsigned)ZP - a0 / (unsigned)ZP + 1) : 0;
     }
     __device__ __forceinline__ Item item(int k) const
     {
+        if (ng > 0) {
+            const int it = (int)blockIdx.x + k * (int)gridDim.x, grp = it % ng;
+            return Item{map, out, n, seg_begin, nseg, it / ng, ZP * grp / ng, ZP * (grp + 1) / ng};
+        }
         const unsigned a0 = u0(), a1 = u1();
         const int sp = (int)(a0 / (unsigned)ZP) + k;
         const unsigned b0 = (unsigned)sp * (unsigned)ZP, e0 = b0 + (unsigned)ZP;
@@ -853,6 +863,10 @@ cudaError_t launch_tc2_pretransform(const float2 *h32, int M, int K, const doubl
 // Template-pair groups per segment pair: the fewest waves of (one block per SM) x the items'
 // length in template pairs plus about two pairs of fixed cost (the two forward FFTs and the
 // pipeline fill and drain).
+// Fewer units than this per block (a few template pairs) and a block's share would cross a
+// segment pair for a handful of units, doubling its forward FFTs: short arrays take groups.
+constexpr int kMinUnitsPerBlock = 12;
+
 static int tc2_groups(int64_t n_sp, int ZP, int sms)
 {
     int best_ng = 1;
@@ -939,12 +953,20 @@ cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsi
     src.nseg = nseg;
     src.n_sp = (nseg + 1) / 2;
     src.ZP = a.ZP;
-    a.ng = 1;   // not used: the blocks split the (segment pair, template pair) units evenly
     const int64_t units = (int64_t)src.n_sp * a.ZP;
     if (units >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-    const int grid = (int)(units < sms ? units : sms);
-    src.q = (int)(units / grid);
-    src.r = (int)(units % grid);
+    int grid;
+    if (units >= (int64_t)kMinUnitsPerBlock * sms) {   // equal unit shares
+        a.ng = src.ng = 0;
+        grid = sms;
+        src.q = (int)(units / grid);
+        src.r = (int)(units % grid);
+    } else {   // short array: whole groups of template pairs of one segment pair per item
+        a.ng = src.ng = tc2_groups(src.n_sp, a.ZP, sms);
+        const int64_t items = (int64_t)src.n_sp * src.ng;
+        grid = (int)(items < sms ? items : sms);
+        src.q = src.r = 0;
+    }
     if (a.cand) ols_tc2_kernel<true><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     else ols_tc2_kernel<false><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     return cudaGetLastError();
