@@ -117,18 +117,16 @@ struct Item {
     int seg_begin, nseg;        // the segments [seg_begin, seg_begin + nseg) this launch covers
     int sp, zp0, zp1;
 };
-// One array (fdas_convolve).  ng = 0: the n_sp x ZP (segment pair, template pair) units in
-// order, an equal share per block (q units, one more for the first r blocks), cut into items
-// at segment-pair boundaries; a segment pair split between two blocks has its forward FFTs
-// done by both (the unit count fits 32 bits: the launcher checks it).  ng > 0 (short arrays,
-// a few units per block): items (segment pair, one of ng template-pair groups) in turn by
-// block, so that no block crosses a segment pair.
+// One array (fdas_convolve): the n_sp x ZP (segment pair, template pair) units in order, an
+// equal share per block (q units, one more for the first r blocks), cut into items at
+// segment-pair boundaries; a segment pair split between two blocks has its forward FFTs done
+// by both (the unit count fits 32 bits: the launcher checks it).
 struct SingleSrc {
     const CUtensorMap *map;
     float *out;
     int64_t n;
     int seg_begin, nseg, n_sp, ZP;
-    int q, r, ng;
+    int q, r;
     __device__ __forceinline__ unsigned u0() const
     {
         const unsigned b = blockIdx.x;
@@ -137,24 +135,34 @@ struct SingleSrc {
     __device__ __forceinline__ unsigned u1() const { return u0() + (unsigned)q + (blockIdx.x < (unsigned)r ? 1u : 0u); }
     __device__ __forceinline__ int count() const
     {
-        if (ng > 0) {
-            const unsigned items = (unsigned)n_sp * (unsigned)ng, b = blockIdx.x;
-            return b < items ? (int)((items - 1 - b) / gridDim.x + 1) : 0;
-        }
         const unsigned a0 = u0(), a1 = u1();
         return a1 > a0 ? (int)((a1 - 1) / (unsigned)ZP - a0 / (unsigned)ZP + 1) : 0;
     }
     __device__ __forceinline__ Item item(int k) const
     {
-        if (ng > 0) {
-            const int it = (int)blockIdx.x + k * (int)gridDim.x, grp = it % ng;
-            return Item{map, out, n, seg_begin, nseg, it / ng, ZP * grp / ng, ZP * (grp + 1) / ng};
-        }
         const unsigned a0 = u0(), a1 = u1();
         const int sp = (int)(a0 / (unsigned)ZP) + k;
         const unsigned b0 = (unsigned)sp * (unsigned)ZP, e0 = b0 + (unsigned)ZP;
         const int zp0 = (int)((a0 > b0 ? a0 : b0) - b0), zp1 = (int)((a1 < e0 ? a1 : e0) - b0);
         return Item{map, out, n, seg_begin, nseg, sp, zp0, zp1};
+    }
+};
+// A short array (a few units per block): items (segment pair, one of ng template-pair groups)
+// in turn by block, so that no block's share crosses a segment pair.
+struct SingleGroupSrc {
+    const CUtensorMap *map;
+    float *out;
+    int64_t n;
+    int seg_begin, nseg, n_sp, ZP, ng;
+    __device__ __forceinline__ int count() const
+    {
+        const unsigned items = (unsigned)n_sp * (unsigned)ng, b = blockIdx.x;
+        return b < items ? (int)((items - 1 - b) / gridDim.x + 1) : 0;
+    }
+    __device__ __forceinline__ Item item(int k) const
+    {
+        const int it = (int)blockIdx.x + k * (int)gridDim.x, grp = it % ng;
+        return Item{map, out, n, seg_begin, nseg, it / ng, ZP * grp / ng, ZP * (grp + 1) / ng};
     }
 };
 // Many arrays (fdas_convolve_batch): array i owns segment pairs [item_off_i, item_off_i +
@@ -800,11 +808,11 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
 
 // One array: segments [s.seg_begin, s.seg_begin + s.nseg); CAND: the threshold crossings
 // instead of the plane (a separate instantiation, so the plane kernel carries none of it).
-template <bool CAND>
+template <bool CAND, class Src>
 __global__ void __launch_bounds__(tc2::kThreads, 1)
-    ols_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const tc2::Args a, const tc2::SingleSrc s0)
+    ols_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const tc2::Args a, const Src s0)
 {
-    tc2::SingleSrc src = s0;
+    Src src = s0;
     src.map = &tmap;
     tc2_body<CAND>(src, a);
 }
@@ -892,9 +900,11 @@ static cudaError_t tc2_setup(int *sms_out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[dev]) {
-        e = cudaFuncSetAttribute(ols_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(ols_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
+        const void *fns[4] = {(const void *)ols_tc2_kernel<false, tc2::SingleSrc>, (const void *)ols_tc2_kernel<true, tc2::SingleSrc>,
+                              (const void *)ols_tc2_kernel<false, tc2::SingleGroupSrc>,
+                              (const void *)ols_tc2_kernel<true, tc2::SingleGroupSrc>};
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+            e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(ols_tc2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2::Smem::total);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
@@ -945,30 +955,38 @@ cudaError_t launch_ols_tc2(const CUtensorMap *tmap, const OlsArgs &o, const unsi
     a.cand_count = o.cand_count;
     a.cand_max = o.cand_max;
     a.threshold = o.threshold;
-    tc2::SingleSrc src;
-    src.map = nullptr;   // the kernel points it at its own parameter copy of the map
-    src.out = o.out;
-    src.n = o.n;
-    src.seg_begin = o.seg_begin;
-    src.nseg = nseg;
-    src.n_sp = (nseg + 1) / 2;
-    src.ZP = a.ZP;
-    const int64_t units = (int64_t)src.n_sp * a.ZP;
+    const int n_sp = (nseg + 1) / 2;
+    const int64_t units = (int64_t)n_sp * a.ZP;
     if (units >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-    int grid;
     if (units >= (int64_t)kMinUnitsPerBlock * sms) {   // equal unit shares
-        a.ng = src.ng = 0;
-        grid = sms;
-        src.q = (int)(units / grid);
-        src.r = (int)(units % grid);
-    } else {   // short array: whole groups of template pairs of one segment pair per item
-        a.ng = src.ng = tc2_groups(src.n_sp, a.ZP, sms);
-        const int64_t items = (int64_t)src.n_sp * src.ng;
-        grid = (int)(items < sms ? items : sms);
-        src.q = src.r = 0;
+        tc2::SingleSrc src;
+        src.map = nullptr;   // the kernel points it at its own parameter copy of the map
+        src.out = o.out;
+        src.n = o.n;
+        src.seg_begin = o.seg_begin;
+        src.nseg = nseg;
+        src.n_sp = n_sp;
+        src.ZP = a.ZP;
+        src.q = (int)(units / sms);
+        src.r = (int)(units % sms);
+        a.ng = 0;
+        if (a.cand) ols_tc2_kernel<true><<<sms, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
+        else ols_tc2_kernel<false><<<sms, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
+    } else {   // short array: whole template-pair groups of one segment pair per item
+        tc2::SingleGroupSrc src;
+        src.map = nullptr;
+        src.out = o.out;
+        src.n = o.n;
+        src.seg_begin = o.seg_begin;
+        src.nseg = nseg;
+        src.n_sp = n_sp;
+        src.ZP = a.ZP;
+        a.ng = src.ng = tc2_groups(n_sp, a.ZP, sms);
+        const int64_t items = (int64_t)n_sp * src.ng;
+        const int grid = (int)(items < sms ? items : sms);
+        if (a.cand) ols_tc2_kernel<true><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
+        else ols_tc2_kernel<false><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     }
-    if (a.cand) ols_tc2_kernel<true><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
-    else ols_tc2_kernel<false><<<grid, tc2::kThreads, tc2::Smem::total, s>>>(*tmap, a, src);
     return cudaGetLastError();
 }
 
