@@ -205,8 +205,8 @@ int fdas_convolve_host(fdas_plan p, const void *in_c64_host, int64_t n, float *o
  * Enqueues, per group of up to 120 arrays, one replay of the plan's CUDA graph
  * [reset the work counter -> persistent kernel with one block per resident slot].  FP32
  * plans: the kernel's blocks take work items (array, template group, segment) from the
- * counter.  FDAS_PREC_TC_DFT2 plans: one block per SM takes items (array, segment pair,
- * template-pair group) in turn by block index.  Each template's arithmetic is that of
+ * counter.  FDAS_PREC_TC_DFT2 plans: one block per SM takes an equal share of the launch's
+ * (array, segment pair, template pair) units.  Each template's arithmetic is that of
  * fdas_convolve (whatever the grouping), so results equal those of fdas_convolve on each
  * array bit for bit.  Asynchronous.  Calls on one plan are serialised by the library on the
  * host; their kernels run in stream order and must not overlap in time: do not

@@ -18,8 +18,9 @@
 //            n1 + 32 n2: |y|^2 in packed FP32x2, the discard of the first K-1 outputs, and stores
 //            in which a warp writes 32 consecutive outputs (128 contiguous bytes).
 //
-// A work item is a pair of consecutive segments and a range of template pairs; a tile is one
-// template of both segments (stage 1), a pair two tiles (stage 2).  Roles: warps 0-3 run the
+// A work item is a pair of consecutive segments and a range of template pairs (each block an
+// equal share of them); a tile is one template of both segments (stage 1), a pair two tiles
+// (stage 2).  Roles: warps 0-3 run the
 // forward FFTs (FP32, once per segment) and the products, warps 4-7 the twiddles, warps 8-11
 // the power epilogue, warps 12 and 14 issue the stage-1 and stage-2 MMAs, warp 13 the TMA loads;
 // mbarriers connect them.
@@ -356,8 +357,8 @@ __global__ void tc2_pretransform_kernel(const float2 *__restrict__ h32, int M, i
 }  // namespace tc2
 
 // ---------------------------------------------------------------------------------------
-// The segment kernel: one block per SM, work items (segment pair, template-pair range) taken
-// round-robin by block index.
+// The segment kernel: one block per SM, each with its share of the work items (segment pair,
+// template-pair range) from the item source Src.
 // ---------------------------------------------------------------------------------------
 template <bool CAND, class Src>
 __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
@@ -819,8 +820,8 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
 
 // Many arrays, one persistent launch: the same items and arithmetic per array as the
 // single-array kernel, so every plane is bit-identical to that array's fdas_convolve.
-// (Same parameter list as the FP32 batch kernel; the work counter is not used: items are
-// taken round-robin by block index.)
+// (Same parameter list as the FP32 batch kernel; the work counter is not used: each block takes
+// an equal share of the launch's (segment pair, template pair) units.)
 __global__ void __launch_bounds__(tc2::kThreads, 1)
     ols_tc2_batch(const __grid_constant__ BatchTable t, const OlsArgs o, int *counter)
 {
