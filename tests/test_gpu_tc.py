@@ -227,3 +227,21 @@ def test_dft2_served_same_alone_and_in_the_mix(fd, oracle_mod, bank):
         for i in (0, 11, 23):
             assert torch.equal(planes[i], plan.convolve(others[i]))
     compare(mixed.cpu().numpy(), oracle_mod.ols_power(x_np, bank), TOL_TC)
+
+
+@pytest.mark.parametrize("n", [135_000, 137_000, 138_743, 301_000])
+def test_dft2_work_shares(fd, oracle_mod, bank, n):
+    # around the switch between whole template-pair groups per item (short arrays) and equal
+    # shares of (segment pair, template pair) units per block: odd and even segment counts,
+    # shares that start and end inside a segment pair; bits equal to the batched form, which
+    # always shares units out
+    rng = np.random.default_rng(n)
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    with fd.Plan(bank, n_max=n, precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        p = plan.convolve(xd)
+        other = torch.from_numpy(np.ascontiguousarray(x[: n // 3])).cuda()
+        outs = plan.convolve_batch([other, xd])
+        plan.status()
+    assert torch.equal(outs[1], p)
+    compare(p.cpu().numpy(), oracle_mod.ols_power(x, bank), TOL_TC)
