@@ -16,14 +16,15 @@
 //            once per block).  M 128, N 128, K 128: two templates of two segments per MMA.
 //   power    one TMEM lane per (n1, segment, template) holds re and im of its 64 outputs
 //            n1 + 32 n2: |y|^2 in packed FP32x2, the discard of the first K-1 outputs, and stores
-//            in which a warp writes 32 consecutive outputs (128 contiguous bytes).
+//            in which a warp writes 32 consecutive outputs (128 contiguous bytes) -- or, in the
+//            threshold instantiation, the crossings of a threshold as records, no plane.
 //
 // A work item is a pair of consecutive segments and a range of template pairs (each block an
 // equal share of them); a tile is one template of both segments (stage 1), a pair two tiles
-// (stage 2).  Roles: warps 0-3 run the
-// forward FFTs (FP32, once per segment) and the products, warps 4-7 the twiddles, warps 8-11
-// the power epilogue, warps 12 and 14 issue the stage-1 and stage-2 MMAs, warp 13 the TMA loads;
-// mbarriers connect them.
+// (stage 2).  Roles: warps 0-3 run the forward FFTs (FP32, once per segment) and the products,
+// warps 4-7 the twiddles, warps 8-11 the power epilogue, warps 12 and 14 issue the stage-1 and
+// stage-2 MMAs, warp 13 the TMA loads; mbarriers (MMA completions, copies) and named barriers
+// (the handoffs to the MMA warps) connect them.
 //
 // Range: the forward spectrum of each segment is scaled by a power of two chosen from its
 // largest component (|X| < 2^11) and the templates by one power of two per plan (|H| <= 16),
