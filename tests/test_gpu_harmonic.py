@@ -50,11 +50,14 @@ def _sorted(got):
 
 
 @pytest.mark.parametrize("m,n,bin0,H", [(85, 5000, BIN0, 8), (85, 4500, BIN0, 32), (9, 7001, 0, 16),
-                                        (1, 3000, 5, 4), (85, 2300, BIN0, 1), (85, 2048 + BIN0 + 2, BIN0, 2)])
+                                        (1, 3000, 5, 4), (85, 2300, BIN0, 1), (85, 2048 + BIN0 + 2, BIN0, 2),
+                                        (129, 20000, BIN0, 8), (131, 9000, BIN0, 4), (85, 1024 + BIN0 + 1, BIN0, 8),
+                                        (3, 50000, 7, 2)])
 def test_every_defined_sum(fd, oracle_mod, m, n, bin0, H):
     """Thresholds below zero make every defined S_h a record (several tiles, ragged last
     tile, staging overflow): the record set is exactly the oracle's domain, each sum within
-    the FP32 summation bound."""
+    the FP32 summation bound.  Shapes: 129 and 131 rows (|z| up to 64 and 65), a row range
+    that ends one cell past 1024 fundamentals, and a three-row plane."""
     P = synth.noise_plane(m, n, seed=41 + n)
     S = oracle_mod.harmonic_sums(P, bin0, H)
     levels = np.array(oracle_mod.harmonic_levels(H))
