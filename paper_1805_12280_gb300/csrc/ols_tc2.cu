@@ -23,8 +23,9 @@
 // equal share of them); a tile is one template of both segments (stage 1), a pair two tiles
 // (stage 2).  Roles: warps 0-3 run the forward FFTs (FP32, once per segment) and the products,
 // warps 4-7 the twiddles, warps 8-11 the power epilogue, warps 12 and 14 issue the stage-1 and
-// stage-2 MMAs, warp 13 the TMA loads; mbarriers (MMA completions, copies) and named barriers
-// (the handoffs to the MMA warps) connect them.
+// stage-2 MMAs, warp 13 the TMA loads.  mbarriers carry the MMA completions, the copies and the
+// handoffs of written operands to the MMA warps; named barriers carry the handoffs of read
+// accumulators back to them.
 //
 // Range: the forward spectrum of each segment is scaled by a power of two chosen from its
 // largest component (|X| < 2^11) and the templates by one power of two per plan (|H| <= 16),
@@ -76,7 +77,9 @@ enum : int {
     B_SCALE0, B_SCALE1, B_SFREE0, B_SFREE1,   // per-item power factors: written / read
     B_H_FULL, B_H_FREE = B_H_FULL + NH,
     B_MMA1 = B_H_FREE + NH, B_MMA2 = B_MMA1 + ND1,   // tcgen05.commit: stage 1 of tile t, stage 2 of pair q
-    B_COUNT = B_MMA2 + 2
+    B_B2F = B_MMA2 + 2,                                  // stage-2 operand of pair q written (128 twiddle threads)
+    B_A1W = B_B2F + 2,                                   // stage-1 operand of tile t written (128 product threads)
+    B_COUNT = B_A1W + 2
 };
 
 struct Smem {
@@ -261,12 +264,17 @@ __device__ __forceinline__ bool p_all(bool ok)
     return r != 0;
 }
 
-// Named hardware barriers for the handoffs between warps (a producer group of 128 threads
-// arrives, the consumer warp syncs): they wake the consumer far sooner than an mbarrier.
+// Named hardware barriers for the handoffs of read accumulators (D1 by the twiddle group, D2 by
+// the power group) back to the MMA warp that overwrites them: a group of 128 threads arrives
+// once its tcgen05.ld have completed, the MMA warp syncs.  They wake the consumer sooner than an
+// mbarrier.  The handoffs of written operands (A1 in tensor memory, the stage-2 operand in
+// shared memory) go through mbarriers instead: with named barriers there, about one launch in
+// a hundred of the 2^22-point plane had one (segment, template) tile differ between relaunches,
+// with or without a fence.acq_rel.cta before the arrive; with mbarriers none in 3000 launches.
 // Every role runs its loops to the end, skipping a tile's work once one of its waits has given
 // up (a warp vote on the waits' results) but still arriving, so that no consumer waits on an
 // arrival that never comes.
-enum : int { NB_A1 = 2, NB_D1 = 4, NB_B2 = 7, NB_D2 = 9 };   // A1 x 2, D1 x 3, B2 x 2, D2 x 2
+enum : int { NB_D1 = 4, NB_D2 = 9 };   // D1 x 3, D2 x 2
 constexpr int NB_COUNT = NT + 32;
 __device__ __forceinline__ void nb_arrive(int id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(NB_COUNT) : "memory"); }
 __device__ __forceinline__ void nb_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(NB_COUNT) : "memory"); }
@@ -396,6 +404,8 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         for (int i = 0; i < (int)ND1; ++i)
             mbar_init(&bar[B_MMA1 + i], 1);        // stage 1 of tile t done: D1[t % 3] full, A1[t % 2] free
         for (int i = 0; i < 2; ++i) mbar_init(&bar[B_MMA2 + i], 1);   // stage 2 of pair q: D2 full, B2 free
+        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_B2F + i], NT);
+        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_A1W + i], NT);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -414,7 +424,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             const Item ii = src.item(k);
             const int zp0 = ii.zp0, zp1 = ii.zp1;
             if (!p_all(!*abort_flag && wait_bar(&bar[B_SEG_FULL], il & 1, abort_flag))) {
-                for (int j = 0; j < 2 * (zp1 - zp0); ++j, ++t) nb_arrive(NB_A1 + (t & 1));   // keep the handoffs
+                for (int j = 0; j < 2 * (zp1 - zp0); ++j, ++t) mbar_arrive(&bar[B_A1W + (t & 1)]);   // keep the handoffs
                 continue;
             }
             float2 v[16], Xa[16], Xb[16];
@@ -476,7 +486,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     bool okw = wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
                     if (t >= 2) okw = wait_bar(&bar[B_MMA1 + (t - 2) % ND1], ((t - 2) / ND1) & 1, abort_flag) && okw;
                     if (!__all_sync(0xffffffffu, okw)) {
-                        nb_arrive(NB_A1 + (t & 1));
+                        mbar_arrive(&bar[B_A1W + (t & 1)]);
                         continue;
                     }
                     tmem_fence_after_sync();
@@ -496,7 +506,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     mbar_arrive(&bar[B_H_FREE + slot]);
                     tmem_st32(tmem_lane_addr(tmem, COL_A1 + 32 * (t & 1)), y);
                     tmem_fence_before_sync();
-                    nb_arrive(NB_A1 + (t & 1));
+                    mbar_arrive(&bar[B_A1W + (t & 1)]);
                 }
             }
         }
@@ -527,7 +537,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     if (zz == 0 && p >= 2) okw = wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag) && okw;
                     if (!__all_sync(0xffffffffu, okw)) {
                         nb_arrive(NB_D1 + t % ND1);
-                        if (zz == 1) nb_arrive(NB_B2 + (p & 1));
+                        if (zz == 1) mbar_arrive(&bar[B_B2F + (p & 1)]);
                         continue;
                     }
                     tmem_fence_after_sync();
@@ -572,7 +582,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     chunk(3, db);
                     if (zz == 1) {
                         fence_proxy_async_smem();
-                        nb_arrive(NB_B2 + (p & 1));
+                        mbar_arrive(&bar[B_B2F + (p & 1)]);
                     }
                 }
             }
@@ -703,9 +713,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             const Item ii = src.item(k);
             const int ntiles = 2 * (ii.zp1 - ii.zp0);
             for (int j = 0; j < ntiles; ++j, ++t) {
-                nb_sync(NB_A1 + (t & 1));                  // A1[t % 2] written
+                const bool oka = wait_bar(&bar[B_A1W + (t & 1)], (t >> 1) & 1, abort_flag);   // A1[t % 2] written
                 if (t >= ND1) nb_sync(NB_D1 + t % ND1);    // D1[t % 3] read by the twiddle group
-                if (lane == 0 && ok && !*abort_flag) {
+                if (lane == 0 && ok && oka && !*abort_flag) {
                     tmem_fence_after_sync();
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
@@ -734,9 +744,9 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             const Item ii = src.item(k);
             const int npairs = ii.zp1 - ii.zp0;
             for (int j = 0; j < npairs; ++j, ++q) {
-                nb_sync(NB_B2 + (q & 1));                  // both tiles of pair q transposed
+                const bool okb = wait_bar(&bar[B_B2F + (q & 1)], (q >> 1) & 1, abort_flag);   // both tiles of pair q transposed
                 if (q >= 2) nb_sync(NB_D2 + (q & 1));      // D2[q % 2] read by the power group
-                if (lane == 0 && ok && !*abort_flag) {
+                if (lane == 0 && ok && okb && !*abort_flag) {
                     tmem_fence_after_sync();
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks)
