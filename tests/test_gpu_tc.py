@@ -265,3 +265,32 @@ def test_relaunches_bit_identical(fd, bank, precision):
                 differing.append(rep)
         plan.status()
     assert not differing, f"launches whose plane differs from the first: {differing}"
+
+
+def test_dft2_batch_and_threshold_relaunches_stable(fd, bank):
+    # the same for the other two instantiations of the two-stage body: the persistent batch
+    # kernel (units of several arrays shared out per block) and the threshold epilogue (the
+    # records come in launch-dependent order: compared as sorted sets)
+    ns = [1 << 21, (1 << 20) + 12345, 300001]
+    xs = [_rand_dev(n, 5150 + i) for i, n in enumerate(ns)]
+    with fd.Plan(bank, n_max=max(ns), precision=fd.FDAS_PREC_TC_DFT2) as plan:
+        first = [o.clone() for o in plan.convolve_batch(xs)]
+        outs = [torch.full_like(o, -1.0) for o in first]
+        differing = []
+        for rep in range(100):
+            plan.convolve_batch(xs, outs=outs)
+            if not all(torch.equal(o, f) for o, f in zip(outs, first)):
+                differing.append(rep)
+        assert not differing, f"batch launches whose planes differ from the first: {differing}"
+
+        def records():   # noise of mean power 2 through unit-norm templates: ~160k crossings of 14
+            buf, count = plan.candidates(xs[0], threshold=14.0, max_cand=1 << 20)
+            assert int(count.item()) < buf.shape[0]   # none dropped, so the set is launch-independent
+            c = fd.candidates_to_numpy(buf, count)
+            return c[np.lexsort((c["bin"], c["tpl"]))]
+
+        ref = records()
+        assert ref.size > 10000
+        for rep in range(30):
+            np.testing.assert_array_equal(records(), ref)
+        plan.status()
