@@ -399,13 +399,15 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
         mbar_init(&bar[B_SFREE1], 4);
         for (int i = 0; i < NH; ++i) {
             mbar_init(&bar[B_H_FULL + i], 1);
-            mbar_init(&bar[B_H_FREE + i], NT);
+            mbar_init(&bar[B_H_FREE + i], 4);   // one lane per product warp
         }
         for (int i = 0; i < (int)ND1; ++i)
             mbar_init(&bar[B_MMA1 + i], 1);        // stage 1 of tile t done: D1[t % 3] full, A1[t % 2] free
         for (int i = 0; i < 2; ++i) mbar_init(&bar[B_MMA2 + i], 1);   // stage 2 of pair q: D2 full, B2 free
-        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_B2F + i], NT);
-        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_A1W + i], NT);
+        // the written-operand and template-free handoffs: one elected lane per producer warp
+        // arrives after a __syncwarp, so 4 arrivals instead of 128 shared atomics per handoff
+        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_B2F + i], 4);
+        for (int i = 0; i < 2; ++i) mbar_init(&bar[B_A1W + i], 4);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -424,7 +426,8 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
             const Item ii = src.item(k);
             const int zp0 = ii.zp0, zp1 = ii.zp1;
             if (!p_all(!*abort_flag && wait_bar(&bar[B_SEG_FULL], il & 1, abort_flag))) {
-                for (int j = 0; j < 2 * (zp1 - zp0); ++j, ++t) mbar_arrive(&bar[B_A1W + (t & 1)]);   // keep the handoffs
+                for (int j = 0; j < 2 * (zp1 - zp0); ++j, ++t)   // keep the handoffs
+                    if (lane == 0) mbar_arrive(&bar[B_A1W + (t & 1)]);
                 continue;
             }
             float2 v[16], Xa[16], Xb[16];
@@ -486,7 +489,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     bool okw = wait_bar(&bar[B_H_FULL + slot], (t / NH) & 1, abort_flag);
                     if (t >= 2) okw = wait_bar(&bar[B_MMA1 + (t - 2) % ND1], ((t - 2) / ND1) & 1, abort_flag) && okw;
                     if (!__all_sync(0xffffffffu, okw)) {
-                        mbar_arrive(&bar[B_A1W + (t & 1)]);
+                        if (lane == 0) mbar_arrive(&bar[B_A1W + (t & 1)]);
                         continue;
                     }
                     tmem_fence_after_sync();
@@ -503,10 +506,12 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                             y[4 * c + i] = *reinterpret_cast<const uint32_t *>(&r);
                         }
                     }
-                    mbar_arrive(&bar[B_H_FREE + slot]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar[B_H_FREE + slot]);
                     tmem_st32(tmem_lane_addr(tmem, COL_A1 + 32 * (t & 1)), y);
                     tmem_fence_before_sync();
-                    mbar_arrive(&bar[B_A1W + (t & 1)]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar[B_A1W + (t & 1)]);
                 }
             }
         }
@@ -537,7 +542,7 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     if (zz == 0 && p >= 2) okw = wait_bar(&bar[B_MMA2 + (p & 1)], ((p - 2) >> 1) & 1, abort_flag) && okw;
                     if (!__all_sync(0xffffffffu, okw)) {
                         nb_arrive(NB_D1 + t % ND1);
-                        if (zz == 1) mbar_arrive(&bar[B_B2F + (p & 1)]);
+                        if (zz == 1 && lane == 0) mbar_arrive(&bar[B_B2F + (p & 1)]);
                         continue;
                     }
                     tmem_fence_after_sync();
@@ -582,7 +587,8 @@ __device__ __forceinline__ void tc2_body(const Src &src, const tc2::Args &a)
                     chunk(3, db);
                     if (zz == 1) {
                         fence_proxy_async_smem();
-                        mbar_arrive(&bar[B_B2F + (p & 1)]);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&bar[B_B2F + (p & 1)]);
                     }
                 }
             }
